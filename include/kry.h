@@ -1,0 +1,138 @@
+/*
+ * kry.h -- C ABI of the GB300 Krylov return-probability library (libkry_gb300.so).
+ *
+ * The library evaluates |psi(t)> = exp(-iHt)|psi0> and the return probability
+ * P(t) = |<psi0|psi(t)>|^2 (Eq. SP, Sec. 4 of Brenes, Varma, Scardicchio, Girotto,
+ * "Massively parallel implementation and approaches to simulate quantum dynamics using
+ * Krylov subspace techniques") for the chain of Eq. 1, restricted to a sector of fixed
+ * particle number N (Sec. 2, "Basis representation"), with Krylov subspaces (Sec. 2,
+ * "Krylov subspace methods").  Everything runs on one CUDA device.
+ *
+ * Conventions shared by every call:
+ *  - A state is an integer: bit i-1 is the occupation (spin up) of site i (Sec. 2).  The
+ *    sector basis is the ascending list of the L-bit integers with N set bits; the rank of
+ *    a state is its index in that list.
+ *  - Hamiltonian (Eq. 1 written in spin-1/2 form, hard-core bosons = XXZ chain):
+ *        H = J sum_b [ (S+_i S-_j + S-_i S+_j)/2 + Delta Sz_i Sz_j ] + sum_i h_i Sz_i,
+ *    Sz = n - 1/2.  Bonds b = (i, i+1), i = 1..L-1, plus (L, 1) when boundary == KRY_PBC
+ *    and L >= 3.  Eq. 1's t and V are J/2 and J*Delta; its on-site term h n_i equals
+ *    h_i Sz_i up to a constant, which does not change P.
+ *  - Pointers named d_* are device pointers, others are host pointers.  All buffers are
+ *    owned by the caller; the library never frees them.  Handles are owned by the library
+ *    and released by the matching *_destroy call.
+ *  - Complex vectors are interleaved (re, im): complex128 (KRY_C128) or complex64
+ *    (KRY_C64).  Vectors of a Hamiltonian with K field rows are stored state-major,
+ *    element (state r, realisation k) at index r*K + k.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *    that return host results synchronise that stream before returning.
+ *  - Every call returns a status code; on failure kry_last_error() gives a message.  No
+ *    C++ exception crosses this interface.  A handle must not be used by two host threads
+ *    at the same time.
+ */
+#ifndef KRY_H
+#define KRY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kry_basis_s *kry_basis;
+typedef struct kry_ham_s *kry_ham;
+
+enum {
+    KRY_OK = 0,
+    KRY_EINVAL = 1,    /* bad argument (size, pointer, state outside the sector, ...) */
+    KRY_ENOMEM = 2,    /* device allocation failed or exceeds the configured cap        */
+    KRY_ETOL = 3,      /* no step size meets the tolerance                              */
+    KRY_ETIMEOUT = 4,  /* the evolution did not finish within its step budget           */
+    KRY_ECUDA = 5      /* a CUDA runtime call failed                                    */
+};
+enum { KRY_OBC = 0, KRY_PBC = 1 };
+enum { KRY_C128 = 0, KRY_C64 = 1 };
+
+/* Counters of one kry_evolve / kry_return_probability call. */
+typedef struct kry_stats {
+    int64_t n_hv;            /* H.v applications (each over all K realisations)            */
+    int64_t n_krylov_steps;  /* accepted time steps                                         */
+    int64_t n_second_pass;   /* reorthogonalisation corrections applied                     */
+    int64_t n_breakdowns;    /* Krylov spaces that became invariant before m vectors        */
+    double err_estimate;     /* sum of the accepted local error estimates (bound on ||dpsi||) */
+    double max_orth_loss;    /* max |<v_i, v_j>| / ||v_j|| seen before the correction        */
+    double time_ms;          /* device time of the call (CUDA events)                        */
+    double algo_bytes;       /* algorithmic HBM bytes of the call, by formula                 */
+} kry_stats;
+
+/* ---------------------------------------------------------------- basis (Sec. 2, Alg. 2)
+ * Create the sector basis of L sites and n_up particles: 1 <= L <= 32, 0 <= n_up <= L.
+ * No basis list is stored; rank and unrank tables of about 2^(L/2+2) bytes live on the
+ * current device.  Returns KRY_EINVAL for bad sizes, KRY_ENOMEM/KRY_ECUDA on device
+ * failure. */
+int kry_basis_create(int L, int n_up, kry_basis *out);
+int kry_basis_destroy(kry_basis b);
+/* Sector dimension D = L!/(N!(L-N)!) (Sec. 2); -1 for a NULL handle. */
+int64_t kry_basis_dim(kry_basis b);
+
+/* Rank: d_ranks[i] = index of state d_states[i] in the sorted basis (Sec. 2 "binary
+ * lookup"; computed here without a stored list).  n >= 0 states, device arrays.  Returns
+ * KRY_EINVAL (after the stream is synchronised) if any state has bits at or above L or a
+ * particle number other than n_up; its rank is then written as 0xFFFFFFFF. */
+int kry_basis_rank(kry_basis b, const uint64_t *d_states, uint32_t *d_ranks, int64_t n,
+                   void *stream);
+/* Unrank: d_states[i] = the basis state of rank d_ranks[i] (the d_ranks[i]-th element of
+ * the list that Algorithm 2 generates).  Ranks >= D give state 0 and KRY_EINVAL. */
+int kry_basis_unrank(kry_basis b, const uint32_t *d_ranks, uint64_t *d_states, int64_t n,
+                     void *stream);
+
+/* ---------------------------------------------------------------- Hamiltonian (Eq. 1)
+ * Bind couplings to a basis.  h: host array [K][L] of on-site fields (row k is
+ * realisation k; K >= 1; the quasiperiodic field of Eq. 1 is h_i = h cos(2 pi beta i +
+ * phi)).  boundary: KRY_OBC or KRY_PBC.  The matrix is never stored: H.v is evaluated
+ * on the fly.  The basis must outlive the Hamiltonian. */
+int kry_hamiltonian_set(kry_basis b, double J, double Delta, const double *h, int K,
+                        int boundary, kry_ham *out);
+int kry_hamiltonian_destroy(kry_ham H);
+
+/* y = H x (the operation H|Psi> of Sec. 2), device vectors of D*K elements of type
+ * dtype.  x and y must not overlap. */
+int kry_apply(kry_ham H, int dtype, const void *d_x, void *d_y, void *stream);
+
+/* Time evolution (Sec. 2, Krylov subspace methods; Eq. SP).  d_psi0: device [D][K]
+ * vector of type dtype (normalised per realisation for P to be a probability).  times:
+ * host array of n_times >= 1 non-decreasing, non-negative output times.  m: Krylov
+ * dimension, 1 <= m <= 32.  tol: absolute error budget of P at every output time.
+ * P_out: host [n_times][K], P_out[t*K+k] = |<psi0_k|psi_k(t)>|^2.  d_psi_out (nullable):
+ * device [D][K] vector receiving psi(times[n_times-1]).  stats nullable.
+ * KRY_C64 keeps vectors and H.v in complex64 and the Lanczos coefficients, dot products,
+ * small exponential and step control in FP64. */
+int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double *times, int n_times,
+               int m, double tol, void *d_psi_out, double *P_out, kry_stats *stats,
+               void *stream);
+
+/* Same as kry_evolve with psi0 = the basis state psi0_state (e.g. the Neel state
+ * ...010101 of Sec. 4) for every realisation; no input vector is needed. */
+int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const double *times,
+                           int n_times, int m, double tol, double *P_out,
+                           kry_stats *stats, void *stream);
+
+/* Small-exponential kernel exposed for testing (Sec. 2: psi ~ V_m exp(-itA_m) e_1).
+ * Given the symmetric tridiagonal T (alpha[m] diagonal, beta[m-1] off-diagonal, host
+ * arrays), its coupling h to the next Krylov vector, and tau >= 0, computes on the
+ * device y = exp(-i tau T) e_1 (host y_out[2m], interleaved) and the local error
+ * estimate err = h |e_m^T tau phi_1(-i tau (T - c)) e_1| used by the step control, with c
+ * the centre of T's Gershgorin interval.  1 <= m <= 32.  Synchronises `stream`. */
+int kry_tridiag_expv(const double *alpha, const double *beta, int m, double h, double tau,
+                     double *y_out, double *err_out, void *stream);
+
+/* Bytes of device workspace kry_evolve allocates for (H, dtype, m); -1 on bad input. */
+int64_t kry_workspace_size(kry_ham H, int dtype, int m);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *kry_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRY_H */

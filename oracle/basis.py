@@ -124,3 +124,26 @@ class CSR:
             for k in range(self.rowptr[r], self.rowptr[r + 1]):
                 H[r, self.col[k]] += self.val[k]
         return H
+
+
+def row_apply(L, J, Delta, h, pbc, b: np.ndarray, x: np.ndarray, rows) -> np.ndarray:
+    """(H x)[r] for the selected rows r only, from the explicit sorted basis b.
+
+    Same construction as CSR (Eq. 1 by bit operations, column by binary lookup), one row
+    at a time, for sizes whose full CSR matrix does not fit in host memory.
+    """
+    l = lib()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    bp = _p(b, ctypes.c_uint64)
+    bonds = [(i, i + 1) for i in range(L - 1)] + ([(L - 1, 0)] if pbc and L >= 3 else [])
+    out = np.zeros(len(rows), dtype=np.complex128)
+    for k, r in enumerate(rows):
+        s = int(b[r])
+        acc = l.orc_diag(ctypes.c_uint64(s), L, float(J), float(Delta), _p(h, ctypes.c_double),
+                         int(pbc)) * x[r]
+        for (i, j) in bonds:
+            if ((s >> i) & 1) != ((s >> j) & 1):
+                c = int(l.orc_lookup(bp, b.size, ctypes.c_uint64(s ^ ((1 << i) | (1 << j)))))
+                acc += 0.5 * J * x[c]
+        out[k] = acc
+    return out

@@ -1,0 +1,215 @@
+"""Python binding of libkry_gb300.so (C ABI in include/kry.h).
+
+Argument marshalling only: every step of the Krylov path runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current stream.  There is no fallback:
+if the library is missing or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libkry_gb300.so")
+
+KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ETOL, KRY_ETIMEOUT, KRY_ECUDA = range(6)
+KRY_OBC, KRY_PBC = 0, 1
+KRY_C128, KRY_C64 = 0, 1
+MMAX = 32
+
+# Every symbol the header declares, with (restype, argtypes).
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Stats(ctypes.Structure):
+    """kry_stats: counters of one evolution."""
+    _fields_ = [("n_hv", ctypes.c_int64), ("n_krylov_steps", ctypes.c_int64),
+                ("n_second_pass", ctypes.c_int64), ("n_breakdowns", ctypes.c_int64),
+                ("err_estimate", ctypes.c_double), ("max_orth_loss", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+SIGNATURES = {
+    "kry_basis_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
+    "kry_basis_destroy": (_i, [_vp]),
+    "kry_basis_dim": (_i64, [_vp]),
+    "kry_basis_rank": (_i, [_vp, _vp, _vp, _i64, _vp]),
+    "kry_basis_unrank": (_i, [_vp, _vp, _vp, _i64, _vp]),
+    "kry_hamiltonian_set": (_i, [_vp, _d, _d, _dp, _i, _i, ctypes.POINTER(_vp)]),
+    "kry_hamiltonian_destroy": (_i, [_vp]),
+    "kry_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "kry_evolve": (_i, [_vp, _i, _vp, _dp, _i, _i, _d, _vp, _dp, ctypes.POINTER(Stats), _vp]),
+    "kry_return_probability": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp,
+                                    ctypes.POINTER(Stats), _vp]),
+    "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
+    "kry_workspace_size": (_i64, [_vp, _i, _i]),
+    "kry_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class KryError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kry error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_1704_02770_gb300.build.build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != KRY_OK:
+        raise KryError(rc, load().kry_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.complex128:
+        return KRY_C128
+    if t.dtype == torch.complex64:
+        return KRY_C64
+    raise TypeError(f"unsupported dtype {t.dtype}: use complex128 or complex64")
+
+
+def _dev_ptr(t, n=None):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_doubles(x):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(_dp)
+
+
+class Basis:
+    """Sector of L sites with n_up particles (Sec. 2); rank/unrank without a stored list."""
+
+    def __init__(self, L: int, n_up: int):
+        lib = load()
+        h = _vp()
+        _check(lib.kry_basis_create(L, n_up, ctypes.byref(h)))
+        self._h, self.L, self.n_up = h, L, n_up
+        self.dim = int(lib.kry_basis_dim(h))
+
+    def rank(self, states, stream=None):
+        import torch
+        out = torch.empty(states.numel(), dtype=torch.int32, device=states.device)
+        _check(load().kry_basis_rank(self._h, _dev_ptr(states), _dev_ptr(out), states.numel(),
+                                     _stream(stream)))
+        return out
+
+    def unrank(self, ranks, stream=None):
+        import torch
+        out = torch.empty(ranks.numel(), dtype=torch.int64, device=ranks.device)
+        _check(load().kry_basis_unrank(self._h, _dev_ptr(ranks), _dev_ptr(out), ranks.numel(),
+                                       _stream(stream)))
+        return out
+
+    def close(self):
+        if self._h:
+            load().kry_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    """Eq. 1 (XXZ form) bound to a basis; fields h has shape [K][L] or [L]."""
+
+    def __init__(self, basis: Basis, J: float, Delta: float, h, pbc: bool = True):
+        import numpy as np
+        hh = np.atleast_2d(np.asarray(h, dtype=np.float64))
+        if hh.shape[1] != basis.L:
+            raise ValueError("h must have L columns")
+        self.K = hh.shape[0]
+        arr, ptr = _host_doubles(hh.ravel())
+        hnd = _vp()
+        _check(load().kry_hamiltonian_set(basis._h, float(J), float(Delta), ptr, self.K,
+                                          KRY_PBC if pbc else KRY_OBC, ctypes.byref(hnd)))
+        self._h, self.basis, self.J, self.Delta, self.h, self.pbc = hnd, basis, J, Delta, hh, pbc
+
+    def apply(self, x, out=None, stream=None):
+        import torch
+        y = torch.empty_like(x) if out is None else out
+        n = self.basis.dim * self.K
+        _check(load().kry_apply(self._h, _dtype_code(x), _dev_ptr(x, n), _dev_ptr(y, n), _stream(stream)))
+        return y
+
+    def evolve(self, psi0, times, m: int = 30, tol: float = 1e-10, psi_out=None, stream=None):
+        import numpy as np
+        t, tp = _host_doubles(times)
+        P = np.zeros(t.size * self.K)
+        st = Stats()
+        n = self.basis.dim * self.K
+        _check(load().kry_evolve(self._h, _dtype_code(psi0), _dev_ptr(psi0, n), tp, t.size, m, tol,
+                                 _dev_ptr(psi_out, n) if psi_out is not None else None,
+                                 P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
+        return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
+
+    def return_probability(self, state: int, times, m: int = 30, tol: float = 1e-10,
+                           dtype: str = "c128", stream=None):
+        import numpy as np
+        t, tp = _host_doubles(times)
+        P = np.zeros(t.size * self.K)
+        st = Stats()
+        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        _check(load().kry_return_probability(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
+                                             P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
+        return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
+
+    def workspace_size(self, dtype: str = "c128", m: int = 30) -> int:
+        return int(load().kry_workspace_size(self._h, KRY_C64 if dtype == "c64" else KRY_C128, m))
+
+    def close(self):
+        if self._h:
+            load().kry_hamiltonian_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tridiag_expv(alpha, beta, h: float, tau: float, stream=None):
+    """Device small exponential: returns (y = exp(-i tau T) e_1, err estimate)."""
+    import numpy as np
+    a, ap = _host_doubles(alpha)
+    b, bp = _host_doubles(beta if len(beta) else [0.0])
+    y = np.zeros(2 * a.size)
+    err = np.zeros(1)
+    _check(load().kry_tridiag_expv(ap, bp, a.size, float(h), float(tau), y.ctypes.data_as(_dp),
+                                   err.ctypes.data_as(_dp), _stream(stream)))
+    return y[0::2] + 1j * y[1::2], float(err[0])

@@ -1,0 +1,200 @@
+// Device helpers of the GB300 Krylov library: rank lookups, the matrix-free H.v row,
+// complex arithmetic and dot-product accumulators.
+#pragma once
+
+#include "kry_internal.cuh"
+
+namespace kry {
+
+// ---------------------------------------------------------------- element types
+
+template <class V> struct VT;
+template <> struct VT<double2> {
+    using R = double;
+    __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ __forceinline__ static double ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_d + p); }
+    __device__ __forceinline__ static double ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_d + p); }
+    __device__ __forceinline__ static double2 from(double2 c) { return c; }
+};
+template <> struct VT<float2> {
+    using R = float;
+    __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ __forceinline__ static float ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_f + p); }
+    __device__ __forceinline__ static float ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_f + p); }
+    __device__ __forceinline__ static float2 from(double2 c) { return make_float2((float)c.x, (float)c.y); }
+};
+
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// w - c v (complex)
+__device__ __forceinline__ double2 cfms(double2 c, double2 v, double2 w)
+{
+    return make_double2(fma(-c.x, v.x, fma(c.y, v.y, w.x)), fma(-c.x, v.y, fma(-c.y, v.x, w.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 c, float2 v, float2 w)
+{
+    return make_float2(fmaf(-c.x, v.x, fmaf(c.y, v.y, w.x)), fmaf(-c.x, v.y, fmaf(-c.y, v.x, w.y)));
+}
+
+// d x + s acc  (real d, s)
+__device__ __forceinline__ double2 axpby(double d, double2 x, double s, double2 a)
+{
+    return make_double2(fma(d, x.x, s * a.x), fma(d, x.y, s * a.y));
+}
+__device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a)
+{
+    return make_float2(fmaf(d, x.x, s * a.x), fmaf(d, x.y, s * a.y));
+}
+__device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
+
+// ---------------------------------------------------------------- dot accumulators
+// sum conj(a) b.  complex128: FP64 fused multiply-adds.  complex64: every product is
+// split exactly (p = a*b rounded, e = fma(a, b, -p)) and summed with Knuth's TwoSum into a
+// float pair (s, c), so the accumulation error is of order 2^-48 of the sum of |terms|
+// and the per-thread result is handed on in FP64.
+
+struct DotAccD {
+    double re = 0.0, im = 0.0;
+    __device__ __forceinline__ void add(double2 a, double2 b)
+    {
+        re = fma(a.x, b.x, re); re = fma(a.y, b.y, re);
+        im = fma(a.x, b.y, im); im = fma(-a.y, b.x, im);
+    }
+    __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+__device__ __forceinline__ void exact_fma(float a, float b, float &s, float &c)
+{
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    float t, err;
+    two_sum(s, p, t, err);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+struct DotAccF {
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    __device__ __forceinline__ void add(float2 a, float2 b)
+    {
+        exact_fma(a.x, b.x, sr, cr); exact_fma(a.y, b.y, sr, cr);
+        exact_fma(a.x, b.y, si, ci); exact_fma(-a.y, b.x, si, ci);
+    }
+    __device__ __forceinline__ double2 value() const
+    {
+        return make_double2((double)sr + (double)cr, (double)si + (double)ci);
+    }
+};
+template <class V> struct DotAcc;
+template <> struct DotAcc<double2> : DotAccD {};
+template <> struct DotAcc<float2> : DotAccF {};
+
+__device__ __forceinline__ double2 warp_sum(double2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- rank tables
+
+__device__ __forceinline__ uint32_t find_block(const DevBasis &b, uint32_t r)
+{
+    uint32_t lo = 0, cnt = 1u << b.Lhi;
+    while (cnt > 0) {
+        uint32_t step = cnt >> 1;
+        if (__ldg(b.blk + lo + step) <= r) { lo += step + 1; cnt -= step + 1; }
+        else cnt = step;
+    }
+    return lo - 1;
+}
+
+// Locate rank r0 + t (< D) as (block hi, offset in block, particles in the lower part).
+__device__ __forceinline__ void tile_unrank(const DevBasis &b, const uint32_t *bsz_s, uint32_t r0,
+                                            uint32_t t, uint32_t &hi, uint32_t &off, int &klo)
+{
+    const uint32_t nhi = 1u << b.Lhi;
+    uint32_t h = find_block(b, r0);
+    uint32_t o = r0 - __ldg(b.blk + h) + t;
+    int k = b.N - __popc(h);
+    while (o >= bsz_s[k]) {
+        o -= bsz_s[k];
+        do { ++h; k = b.N - __popc(h); } while ((k < 0 || k > b.Llo) && h + 1 < nhi);
+        if (k < 0 || k > b.Llo) { k = 0; o = 0; break; }   // unreachable when r0 + t < D
+    }
+    hi = h; off = o; klo = k;
+}
+
+// Stage the small tables (and optionally ranklo, 2^Llo 16-bit entries) in shared memory.
+__device__ __forceinline__ void stage_tables(const DevBasis &b, uint32_t *koff_s, uint32_t *bsz_s,
+                                             uint16_t *rl_s, int rl_smem)
+{
+    for (int i = threadIdx.x; i < b.Llo + 2; i += blockDim.x) koff_s[i] = __ldg(b.koff + i);
+    for (int i = threadIdx.x; i < b.Llo + 1; i += blockDim.x) bsz_s[i] = __ldg(b.bsz + i);
+    if (rl_smem) {
+        const uint32_t n2 = (1u << b.Llo) >> 1;   // Llo >= 1, so the count is even
+        const uint32_t *src = (const uint32_t *)b.ranklo;
+        uint32_t *dst = (uint32_t *)rl_s;
+        for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+}
+
+// ---------------------------------------------------------------- matrix-free H.v
+// Row r of H x for the state s = (hi << Llo) | lo (Eq. 1, XXZ form):
+//   (H x)[r] = d(s) x[r] + (J/2) sum_{antiparallel bonds b} x[rank(s ^ bondmask_b)],
+//   d(s) = (J Delta / 4)(nbonds - 2 n_anti(s)) + sum_i h_i (n_i - 1/2).
+// Pull form (one writer per row, no atomics).  The re-rank of a hopped state takes two
+// table lookups; a hop inside the upper part keeps the lower bits, so its target is
+// blk[hi'] + off and the lanes of one block read consecutive elements.
+template <class V>
+__device__ __forceinline__ V hv_row(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
+                                    uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
+                                    const uint16_t *rl)
+{
+    using R = typename VT<V>::R;
+    const int Llo = b.Llo, L = b.L;
+    const uint32_t pos = koff_s[klo] + off;
+    const uint32_t lo = __ldg(b.lolist + pos);
+    const uint32_t s = (hi << Llo) | lo;
+    const uint32_t base = __ldg(b.blk + hi);
+    const uint32_t lomask = (1u << Llo) - 1u;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint32_t anti = (s ^ (s >> 1)) & obc;
+    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
+    const int nanti = __popc(anti) + (int)wrap;
+    const R d = (R)hm.cz * (R)(hm.nbonds - 2 * nanti) + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
+    V acc = VT<V>::zero();
+    uint32_t a = anti & ((1u << (Llo - 1)) - 1u);          // bonds inside the lower part
+    while (a) {
+        const int p = __ffs(a) - 1;
+        a &= a - 1u;
+        acc = acc + __ldg(x + base + rl[lo ^ (3u << p)]);
+    }
+    if (b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u)) {         // bond joining the two parts
+        const uint32_t s2 = s ^ (3u << (Llo - 1));
+        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    uint32_t ah = anti >> Llo;                              // bonds inside the upper part
+    while (ah) {
+        const int q = __ffs(ah) - 1;
+        ah &= ah - 1u;
+        acc = acc + __ldg(x + __ldg(b.blk + (hi ^ (3u << q))) + off);
+    }
+    if (wrap) {                                             // ring bond (L-1, 0)
+        const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
+        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    return axpby(d, __ldg(x + base + off), (R)hm.halfJ, acc);
+}
+
+}  // namespace kry

@@ -1,0 +1,302 @@
+// Host side of the time evolution (Sec. 2, "Krylov subspace methods"; Eq. SP): workspace,
+// CUDA-graph capture of one Krylov step, the replay loop and the C ABI entry points
+// kry_apply / kry_evolve / kry_return_probability.
+//
+// One Krylov step, captured once per (precision, m) and replayed:
+//   for j = 0..m-1:  pass A (u = H v_j + dots)  ->  pass B (update + second-pass dots)
+//                    ->  pass C (correction, runs only when flagged)
+//   small exponential + step control + dense output of P  ->  combine psi = beta V y.
+// Device flags end the Lanczos loop early on an invariant subspace and turn every kernel
+// into a no-op once the last output time is reached; the host only polls that flag.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "kry_internal.cuh"
+
+using namespace kry;
+
+namespace {
+
+uint64_t binom_host(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    return r;
+}
+
+size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(double2); }
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int rl_in_smem(const DevBasis &b) { return b.Llo <= 15 ? 1 : 0; }
+
+struct Layout {
+    size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, bytes;
+};
+
+Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
+{
+    Layout l{};
+    const size_t es = elem_size(dtype);
+    const size_t n = (size_t)H->b->D * (size_t)H->K;
+    l.ldW = round_up(n, 64);
+    l.oW = 0;
+    l.oU = l.oW + (size_t)(m + 1) * l.ldW * es;
+    l.oG = l.oU + l.ldW * es;
+    l.oPart = l.oG + l.ldW * es;
+    l.oCtl = round_up(l.oPart + (size_t)grid * PSTRIDE * sizeof(double2), 256);
+    l.oTimes = round_up(l.oCtl + sizeof(KryCtl), 256);
+    l.oP = round_up(l.oTimes + sizeof(double) * (size_t)n_times, 256);
+    l.bytes = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    return l;
+}
+
+int grid_for(const kry_ham_s *H, int dtype)
+{
+    const DevBasis &b = H->b->dev;
+    return dtype == KRY_C64 ? vector_grid<float2>(b, rl_in_smem(b)) : vector_grid<double2>(b, rl_in_smem(b));
+}
+
+void drop_graph(kry_ham_s *H)
+{
+    if (H->gexec) cudaGraphExecDestroy(H->gexec);
+    H->gexec = nullptr;
+}
+
+template <class V>
+int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int grid)
+{
+    cudaStream_t cs = H->cap_stream;
+    cudaGraph_t g = nullptr;
+    KRY_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = KRY_OK;
+    for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
+        rc = launch_passA<V>(a, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, grid, cs);
+    }
+    if (rc == KRY_OK) rc = launch_smallexp(ea, cs);
+    if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, grid, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&H->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { H->gexec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return KRY_OK;
+}
+
+template <class V>
+int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool general,
+             const double *times, int n_times, int m, double tol, void *d_psi_out, double *P_out,
+             kry_stats *st, cudaStream_t s)
+{
+    const DevBasis &b = H->b->dev;
+    const int grid = grid_for(H, dtype);
+    if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
+    const Layout l = layout(H, dtype, m, grid, n_times);
+    if (!H->ws || H->ws_bytes < l.bytes) {
+        drop_graph(H);
+        if (H->ws) cudaFree(H->ws);
+        H->ws = nullptr;
+        H->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&H->ws, l.bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+        H->ws_bytes = l.bytes;
+    }
+    if (!H->cap_stream) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    if (!H->h_poll) KRY_CU(cudaMallocHost(&H->h_poll, sizeof(KryCtl)));
+    char *base = (char *)H->ws;
+    EvArgs<V> a{};
+    a.b = b;
+    a.h = H->dev;
+    a.W = (V *)(base + l.oW);
+    a.ldW = l.ldW;
+    a.U = (V *)(base + l.oU);
+    a.G = general ? (const V *)(base + l.oG) : nullptr;
+    a.part = (double2 *)(base + l.oPart);
+    a.ctl = (KryCtl *)(base + l.oCtl);
+    a.rl_smem = rl_in_smem(b);
+    ExpArgs ea{};
+    ea.ctl = a.ctl;
+    ea.times = (const double *)(base + l.oTimes);
+    ea.P = (double *)(base + l.oP);
+    ea.W = a.W;
+    ea.ldW = l.ldW;
+    ea.c64 = dtype == KRY_C64;
+    // graph of one Krylov step (reused while the workspace and the shape are unchanged)
+    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
+                     H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
+                     H->ws_bytes < l.bytes))
+        drop_graph(H);
+    if (!H->gexec) {
+        if (int rc = capture_step<V>(H, a, ea, m, grid)) return rc;
+        H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid;
+        H->g_ws = H->ws; H->g_G = base + l.oP;
+    }
+    cudaEvent_t ev0, ev1;
+    KRY_CU(cudaEventCreate(&ev0));
+    KRY_CU(cudaEventCreate(&ev1));
+    KRY_CU(cudaEventRecord(ev0, s));
+    // control block
+    KryCtl c;
+    std::memset(&c, 0, sizeof c);
+    c.m = m;
+    c.m_eff = m;
+    c.t_end = times[n_times - 1];
+    c.tol = tol;
+    c.n_times = n_times;
+    c.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
+    c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
+    const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)H->K;
+    if (general) {
+        c.r0 = -1;
+    } else {
+        uint64_t r = 0;
+        int j = 0;
+        for (int p = 0; p < b.L; ++p)
+            if ((state >> p) & 1ull) r += binom_host(p, ++j);
+        c.r0 = (int)r;
+        c.beta0 = 1.0;
+        c.sigma[0] = 1.0;
+        c.g[0] = make_double2(1.0, 0.0);
+    }
+    KRY_CU(cudaMemcpyAsync(a.ctl, &c, sizeof c, cudaMemcpyHostToDevice, s));
+    KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
+    if (general) {
+        KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        if (int rc = launch_lincomb<V>(a, 3, 0, grid, s)) return rc;
+    } else {
+        KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
+        if (int rc = launch_set_basis_state(a.W, dtype == KRY_C64, (uint32_t)c.r0, s)) return rc;
+    }
+    // replay until the device reports the last output time
+    KryCtl *hp = (KryCtl *)H->h_poll;
+    long long launched = 0;
+    const long long max_launch = 500000;   // Krylov steps before KRY_ETIMEOUT
+    int batch = 1;
+    for (;;) {
+        for (int i = 0; i < batch; ++i) KRY_CU(cudaGraphLaunch(H->gexec, s));
+        launched += batch;
+        KRY_CU(cudaMemcpyAsync(hp, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, s));
+        KRY_CU(cudaStreamSynchronize(s));
+        if (hp->done) break;
+        if (launched >= max_launch) {
+            set_error("kry_evolve: no convergence after %lld Krylov steps (t = %g of %g)", launched,
+                      hp->t_now, hp->t_end);
+            return KRY_ETIMEOUT;
+        }
+        const double rem = hp->t_end - hp->t_now;
+        const double est = hp->tau_prev > 0.0 ? rem / hp->tau_prev : 1.0;
+        batch = (int)std::min(64.0, std::max(1.0, std::ceil(est * 1.05)));
+    }
+    KRY_CU(cudaEventRecord(ev1, s));
+    if (hp->err) {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
+        else set_error("kry_evolve: initial vector has zero norm");
+        return hp->err;
+    }
+    KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * H->K, cudaMemcpyDeviceToHost, s));
+    if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    KRY_CU(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (st) {
+        st->n_hv = hp->n_hv;
+        st->n_krylov_steps = hp->n_steps;
+        st->n_second_pass = hp->n_corr;
+        st->n_breakdowns = hp->n_bd;
+        st->err_estimate = hp->err_sum;
+        st->max_orth_loss = hp->max_orth;
+        st->time_ms = ms;
+        st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
+    }
+    return KRY_OK;
+}
+
+int check_evolve_args(kry_ham H, int dtype, const double *times, int n_times, int m, double tol,
+                      double *P_out)
+{
+    if (!H || !times || n_times < 1 || !P_out || m < 1 || m > MMAX || !(tol > 0.0) ||
+        (dtype != KRY_C128 && dtype != KRY_C64)) {
+        set_error("kry_evolve: bad arguments (need H, times, n_times >= 1, P_out, 1 <= m <= %d, tol > 0)", MMAX);
+        return KRY_EINVAL;
+    }
+    for (int i = 0; i < n_times; ++i) {
+        if (!(times[i] >= 0.0) || !std::isfinite(times[i]) || (i > 0 && times[i] < times[i - 1])) {
+            set_error("kry_evolve: times must be finite, non-negative and non-decreasing");
+            return KRY_EINVAL;
+        }
+    }
+    return KRY_OK;
+}
+
+}  // namespace
+
+extern "C" int kry_hamiltonian_destroy(kry_ham H)
+{
+    if (!H) return KRY_OK;
+    drop_graph(H);
+    if (H->ws) cudaFree(H->ws);
+    if (H->d_eh) cudaFree(H->d_eh);
+    if (H->h_poll) cudaFreeHost(H->h_poll);
+    if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    delete H;
+    return KRY_OK;
+}
+
+extern "C" int64_t kry_workspace_size(kry_ham H, int dtype, int m)
+{
+    if (!H || m < 1 || m > MMAX || (dtype != KRY_C128 && dtype != KRY_C64)) return -1;
+    const int grid = grid_for(H, dtype);
+    if (grid <= 0) return -1;
+    return (int64_t)layout(H, dtype, m, grid, 1).bytes;
+}
+
+extern "C" int kry_apply(kry_ham H, int dtype, const void *d_x, void *d_y, void *stream)
+{
+    if (!H || !d_x || !d_y || d_x == d_y || (dtype != KRY_C128 && dtype != KRY_C64)) {
+        set_error("kry_apply: bad arguments");
+        return KRY_EINVAL;
+    }
+    const DevBasis &b = H->b->dev;
+    return launch_apply(b, H->dev, dtype == KRY_C64, d_x, d_y, rl_in_smem(b), (cudaStream_t)stream);
+}
+
+extern "C" int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double *times, int n_times,
+                          int m, double tol, void *d_psi_out, double *P_out, kry_stats *stats,
+                          void *stream)
+{
+    if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
+    if (!d_psi0) { set_error("kry_evolve: d_psi0 is NULL"); return KRY_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == KRY_C64)
+        return evolve_t<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+    return evolve_t<double2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+}
+
+extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const double *times,
+                                      int n_times, int m, double tol, double *P_out, kry_stats *stats,
+                                      void *stream)
+{
+    if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
+    const int L = H->b->L;
+    if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
+        set_error("kry_return_probability: state is not in the (L=%d, N=%d) sector", L, H->b->N);
+        return KRY_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == KRY_C64)
+        return evolve_t<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+    return evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+}

@@ -1,0 +1,376 @@
+// Small exponential, error estimate and step control of one Krylov step (Sec. 2:
+// psi(t + tau) ~ beta V_m exp(-i tau T_m) e_1 with time stepping and error estimation),
+// run by one warp in FP64 without a host round trip.
+//
+// T (m_eff x m_eff, symmetric tridiagonal from Lanczos) is shifted and scaled into
+// [-1, 1]: T~ = (T - c)/r with c, r the centre and half-width of its Gershgorin interval.
+// Then (Jacobi-Anger expansion)
+//     exp(-i tau T) e_1 = exp(-i tau c) sum_k w_k J_k(tau r) T_k(T~) e_1,
+//     w_0 = 1, w_k = 2 (-i)^k,
+// with Bessel functions J_k from Miller's backward recurrence normalised by
+// J_0 + 2 sum J_2k = 1.  The leading term of the Krylov error (Saad 1992; the estimate
+// of Sidje's Expokit that the paper relies on) is
+//     err(tau) = beta h |e_m^T tau phi_1(-i tau (T - c)) e_1|
+//              = (beta h / r) |sum_k w_k I_k(tau r) [T_k(T~) e_1]_m|,
+// where I_k(x) = int_0^x J_k = 2 sum_n J_{k+2n+1}(x) (Abramowitz & Stegun 11.1.2) and h is
+// the coupling of v_m to the next Krylov vector.  A ladder of 32 candidate steps (one per
+// lane) is scanned and the largest tau with err(tau) <= 0.05 tol tau / t_end is taken;
+// the Krylov basis is reused, so a rejected candidate costs no H.v.  Every output time in
+// [t, t + tau] is read from the same expansion (dense output):
+//     <psi0|psi(t + tau')> = beta exp(-i tau' c) sum_k w_k J_k(tau' r) sum_j g_j [T_k(T~) e_1]_j,
+// g_j = <psi0|v_j>.
+#include <cuda_runtime.h>
+
+#include "kry_device.cuh"
+
+namespace kry {
+
+constexpr double STEP_SAFETY = 0.1;   // fraction of the local error budget a step may use
+constexpr double LADDER = 0.85;       // ratio of consecutive candidate steps
+
+struct ExpSmem {
+    double al[MMAX], be[MMAX];
+    double2 g[MMAX];
+    double tch[(KMAX + 1) * 32];      // T_k(T~) e_1, component j at [k * 32 + j]
+    double jb[32 * (KMAX + 2)];       // per-lane Bessel sequences
+    double2 gk[KMAX + 1];             // sum_j g_j [T_k(T~) e_1]_j
+};
+
+__device__ __forceinline__ int cheb_degree(double x)
+{
+    const int K = (int)ceil(x + 8.0 * cbrt(x) + 24.0);
+    return K < KMAX ? K : KMAX;
+}
+
+// J_k(x) for k = 0..K into out[0..K] (x >= 0).
+__device__ void bessel_seq(double x, int K, double *out)
+{
+    if (x < 1e-6) {
+        for (int k = 0; k <= K; ++k) out[k] = 0.0;
+        out[0] = 1.0 - 0.25 * x * x;
+        if (K >= 1) out[1] = 0.5 * x - x * x * x / 16.0;
+        if (K >= 2) out[2] = x * x / 8.0;
+        if (K >= 3) out[3] = x * x * x / 48.0;
+        return;
+    }
+    int ns = (K > (int)x ? K : (int)x) + 40;
+    ns += ns & 1;
+    const double inv = 2.0 / x;
+    double jp1 = 0.0, jk = 1e-280, sum = 0.0;
+    for (int k = ns; k >= 1; --k) {
+        const double jm1 = (double)k * inv * jk - jp1;
+        jp1 = jk;
+        jk = jm1;
+        const int idx = k - 1;
+        if (idx <= K) out[idx] = jm1;
+        if (idx >= 2 && !(idx & 1)) sum += jm1;
+        if (fabs(jk) > 1e250) {
+            jk *= 1e-250;
+            jp1 *= 1e-250;
+            sum *= 1e-250;
+            for (int t = idx; t <= K; ++t) out[t] *= 1e-250;
+        }
+    }
+    const double invS = 1.0 / (out[0] + 2.0 * sum);
+    for (int k = 0; k <= K; ++k) out[k] *= invS;
+}
+
+// sum_k w_k c_k v_k as a complex number, for real c_k, v_k
+__device__ __forceinline__ double2 jacobi_anger_sum(const double *c, const double *v, int vstride, int K)
+{
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k <= K; ++k) {
+        const double t = c[k] * v[k * vstride] * (k == 0 ? 1.0 : 2.0);
+        switch (k & 3) {
+        case 0: re += t; break;
+        case 1: im -= t; break;
+        case 2: re -= t; break;
+        default: im += t; break;
+        }
+    }
+    return make_double2(re, im);
+}
+
+// Error-estimate sum: sum_k w_k I_k v_k with I_k = int_0^x J_k from the J sequence.
+__device__ __forceinline__ double2 integral_sum(const double *J, const double *v, int vstride, int K)
+{
+    double re = 0.0, im = 0.0, ip1 = 0.0, ip2 = 0.0;   // I_{k+1}, I_{k+2}
+    for (int k = K; k >= 0; --k) {
+        const double Ik = (k + 1 <= K ? 2.0 * J[k + 1] : 0.0) + ip2;
+        ip2 = ip1;
+        ip1 = Ik;
+        const double t = Ik * v[k * vstride] * (k == 0 ? 1.0 : 2.0);
+        switch (k & 3) {
+        case 0: re += t; break;
+        case 1: im -= t; break;
+        case 2: re -= t; break;
+        default: im += t; break;
+        }
+    }
+    return make_double2(re, im);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Gershgorin centre c and half-width r of T (lanes own rows), then the Chebyshev vectors
+// T_k(T~) e_1 for k = 0..K into sm.tch.  Returns (c, r) in every lane.
+__device__ double2 chebyshev_basis(ExpSmem &sm, int me, int K)
+{
+    const int j = threadIdx.x;
+    const double a = (j < me) ? sm.al[j] : 0.0;
+    const double bl = (j >= 1 && j < me) ? fabs(sm.be[j - 1]) : 0.0;
+    const double br = (j + 1 < me) ? fabs(sm.be[j]) : 0.0;
+    double lo = (j < me) ? a - bl - br : 1e300, hi = (j < me) ? a + bl + br : -1e300;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double c = 0.5 * (lo + hi);
+    double r = 0.5 * (hi - lo);
+    const double rmin = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+    if (!(r > rmin)) r = rmin;
+    const double ir = 1.0 / r;
+    const double dj = (j < me) ? (a - c) * ir : 0.0;
+    const double ol = (j >= 1 && j < me) ? sm.be[j - 1] * ir : 0.0;
+    const double orr = (j + 1 < me) ? sm.be[j] * ir : 0.0;
+    double v0 = (j == 0) ? 1.0 : 0.0;
+    sm.tch[j] = v0;
+    double up = __shfl_up_sync(0xffffffffu, v0, 1), dn = __shfl_down_sync(0xffffffffu, v0, 1);
+    double v1 = dj * v0 + ol * up + orr * dn;
+    if (K >= 1) sm.tch[32 + j] = v1;
+    for (int k = 2; k <= K; ++k) {
+        up = __shfl_up_sync(0xffffffffu, v1, 1);
+        dn = __shfl_down_sync(0xffffffffu, v1, 1);
+        const double v2 = 2.0 * (dj * v1 + ol * up + orr * dn) - v0;
+        sm.tch[k * 32 + j] = v2;
+        v0 = v1;
+        v1 = v2;
+    }
+    __syncwarp();
+    return make_double2(c, r);
+}
+
+__global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
+{
+    KryCtl *ctl = ea.ctl;
+    if (ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ExpSmem &sm = *(ExpSmem *)smem_raw;
+    const int lane = threadIdx.x;
+    const int me = ctl->m_eff;
+    if (lane < me) {
+        sm.al[lane] = ctl->alpha[lane];
+        sm.be[lane] = ctl->beta[lane];
+        double2 g;
+        if (ctl->r0 >= 0) {
+            const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->r0;
+            double2 w;
+            if (ea.c64) { float2 f = ((const float2 *)ea.W)[idx]; w = make_double2(f.x, f.y); }
+            else w = ((const double2 *)ea.W)[idx];
+            // <psi0|v_j> with psi0 = e_{r0}: the (real-valued psi0) conjugate is trivial
+            const double s = ctl->sigma[lane];
+            g = make_double2(w.x * s, w.y * s);
+        } else {
+            g = ctl->g[lane];
+        }
+        sm.g[lane] = g;
+    }
+    __syncwarp();
+    const double beta0 = ctl->beta0, h = sm.be[me - 1];
+    const double t_now = ctl->t_now, t_end = ctl->t_end, tol = ctl->tol;
+    const double remaining = t_end - t_now;
+    // provisional radius for the step cap (recomputed exactly by chebyshev_basis)
+    double2 cr;
+    {
+        const int j = lane;
+        const double a = (j < me) ? sm.al[j] : 0.0;
+        const double bl = (j >= 1 && j < me) ? fabs(sm.be[j - 1]) : 0.0;
+        const double br = (j + 1 < me) ? fabs(sm.be[j]) : 0.0;
+        double lo = (j < me) ? a - bl - br : 1e300, hi = (j < me) ? a + bl + br : -1e300;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        double r = 0.5 * (hi - lo);
+        const double rmin = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+        cr = make_double2(0.5 * (lo + hi), r > rmin ? r : rmin);
+    }
+    const double tau_hi = fmin(remaining, XMAX / cr.y);
+    const int K = cheb_degree(tau_hi * cr.y);
+    cr = chebyshev_basis(sm, me, K);
+    const double c = cr.x, r = cr.y;
+    double *myJ = sm.jb + lane * (KMAX + 2);
+
+    // ---- step-size ladder
+    double tau_top = tau_hi, tau = 0.0, err = 0.0;
+    int pick = -1;
+    for (int round = 0; round < 4 && pick < 0; ++round) {
+        const double tq = tau_top * pow(LADDER, (double)lane);
+        bessel_seq(tq * r, K, myJ);
+        double eq = 0.0;
+        if (h != 0.0) {
+            const double2 s = integral_sum(myJ, sm.tch + (me - 1), 32, K);
+            eq = beta0 * fabs(h) / r * sqrt(s.x * s.x + s.y * s.y);
+        }
+        const bool ok = (tq > 0.0 || remaining <= 0.0) &&
+                        eq <= STEP_SAFETY * 0.5 * tol * tq / t_end;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok || (remaining <= 0.0));
+        if (mask) {
+            pick = __ffs(mask) - 1;
+            tau = __shfl_sync(0xffffffffu, tq, pick);
+            err = __shfl_sync(0xffffffffu, eq, pick);
+        } else {
+            tau_top *= pow(LADDER, 32.0);
+        }
+    }
+    __syncwarp();
+    if (pick < 0) {
+        if (lane == 0) { ctl->err = KRY_ETOL; ctl->done = 1; }
+        return;
+    }
+    const bool last = (tau >= remaining);
+    // ---- y(tau) -> combine coefficients
+    const double *Jp = sm.jb + pick * (KMAX + 2);
+    if (lane < me) {
+        const double2 s = jacobi_anger_sum(Jp, sm.tch + lane, 32, K);
+        double sn, cs;
+        sincos(tau * c, &sn, &cs);
+        const double2 y = cmul(make_double2(cs, -sn), s);
+        const double f = -beta0 * ctl->sigma[lane];
+        ctl->coefY[lane] = make_double2(f * y.x, f * y.y);
+    }
+    // ---- G_k = sum_j g_j [T_k e_1]_j
+    for (int k = lane; k <= K; k += 32) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < me; ++j) {
+            const double t = sm.tch[k * 32 + j];
+            re += sm.g[j].x * t;
+            im += sm.g[j].y * t;
+        }
+        sm.gk[k] = make_double2(re, im);
+    }
+    __syncwarp();
+    // ---- dense output at every output time inside [t_now, t_now + tau]
+    int next = ctl->next_out;
+    const int n_times = ctl->n_times;
+    while (next < n_times) {
+        const int o = next + lane;
+        double tp = 0.0;
+        bool in = false;
+        if (o < n_times) {
+            tp = ea.times[o] - t_now;
+            in = last ? true : (tp <= tau * (1.0 + 1e-12));
+            if (tp < 0.0) tp = 0.0;
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, in);
+        const int cnt = __popc(mk & ~(mk + 1u));   // leading run of lanes (times are sorted)
+        if (lane < cnt) {
+            bessel_seq(tp * r, K, myJ);
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k <= K; ++k) {
+                const double t = myJ[k] * (k == 0 ? 1.0 : 2.0);
+                const double2 G = sm.gk[k];
+                // w_k G_k with w_k = (-i)^k
+                switch (k & 3) {
+                case 0: re += t * G.x; im += t * G.y; break;
+                case 1: re += t * G.y; im -= t * G.x; break;
+                case 2: re -= t * G.x; im -= t * G.y; break;
+                default: re -= t * G.y; im += t * G.x; break;
+                }
+            }
+            double sn, cs;
+            sincos(tp * c, &sn, &cs);
+            const double2 A = cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
+            ea.P[o] = A.x * A.x + A.y * A.y;
+        }
+        next += cnt;
+        if (cnt < 32) break;
+    }
+    if (lane == 0) {
+        ctl->next_out = next;
+        ctl->t_now = last ? t_end : t_now + tau;
+        ctl->tau_prev = tau;
+        ctl->n_steps += 1;
+        ctl->err_sum += err;
+        if (next >= n_times) ctl->finishing = 1;
+    }
+}
+
+// Test hook: y = exp(-i tau T) e_1 and err(tau) for given T, h (beta = 1).
+__global__ void __launch_bounds__(32) k_expv_test(const double *alpha, const double *beta, int me,
+                                                  double h, double tau, double *y, double *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ExpSmem &sm = *(ExpSmem *)smem_raw;
+    const int lane = threadIdx.x;
+    if (lane < me) {
+        sm.al[lane] = alpha[lane];
+        sm.be[lane] = (lane + 1 < me) ? beta[lane] : h;
+    }
+    __syncwarp();
+    // radius first (with K = 0), then the full basis for the needed degree
+    double2 cr = chebyshev_basis(sm, me, 0);
+    const int K = cheb_degree(tau * cr.y);
+    cr = chebyshev_basis(sm, me, K);
+    double *myJ = sm.jb + lane * (KMAX + 2);
+    bessel_seq(tau * cr.y, K, myJ);
+    __syncwarp();
+    const double *J0 = sm.jb;   // lane 0's sequence (all lanes computed the same)
+    if (lane < me) {
+        const double2 s = jacobi_anger_sum(J0, sm.tch + lane, 32, K);
+        double sn, cs;
+        sincos(tau * cr.x, &sn, &cs);
+        const double2 yy = cmul(make_double2(cs, -sn), s);
+        y[2 * lane] = yy.x;
+        y[2 * lane + 1] = yy.y;
+    }
+    if (lane == 0) {
+        const double2 s = integral_sum(J0, sm.tch + (me - 1), 32, K);
+        *err = fabs(h) / cr.y * sqrt(s.x * s.x + s.y * s.y);
+    }
+}
+
+int launch_smallexp(const ExpArgs &a, cudaStream_t s)
+{
+    KRY_CU(cudaFuncSetAttribute(k_smallexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(ExpSmem)));
+    k_smallexp<<<1, 32, sizeof(ExpSmem), s>>>(a);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+}  // namespace kry
+
+using namespace kry;
+
+extern "C" int kry_tridiag_expv(const double *alpha, const double *beta, int m, double h, double tau,
+                                double *y_out, double *err_out, void *stream)
+{
+    if (!alpha || (m > 1 && !beta) || !y_out || !err_out || m < 1 || m > MMAX || !(tau >= 0.0) ||
+        !(tau * 1.0 < 1e300)) {
+        set_error("kry_tridiag_expv: bad arguments");
+        return KRY_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *d = nullptr;
+    KRY_CU(cudaMalloc(&d, sizeof(double) * (4 * MMAX + 2)));
+    double *da = d, *db = d + MMAX, *dy = d + 2 * MMAX, *de = d + 4 * MMAX;
+    cudaMemcpyAsync(da, alpha, sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    if (m > 1) cudaMemcpyAsync(db, beta, sizeof(double) * (m - 1), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaFuncSetAttribute(k_expv_test, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(ExpSmem));
+    if (e == cudaSuccess) {
+        k_expv_test<<<1, 32, sizeof(ExpSmem), s>>>(da, db, m, h, tau, dy, de);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_out, dy, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err_out, de, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "kry_tridiag_expv");
+    return KRY_OK;
+}

@@ -1,0 +1,411 @@
+// Vector kernels of the Krylov step (Sec. 2, "Krylov subspace methods"):
+//   k_apply     y = H x (matrix-free, Eq. 1)
+//   k_passA     u = H v_j fused with all dots <v_i, u>, i <= j (alpha_j and the first
+//               reorthogonalisation pass share one sweep over HBM)
+//   k_lincomb   w = src - sum_i c_i W_i with an optional second sweep of dots
+//               (MODE 0: Lanczos update + second-pass dots; 1: second-pass correction;
+//                2: combine psi = beta V y; 3: load the initial vector)
+// Every reduction ends in the last CTA to finish (ticket counter), which sums the
+// per-CTA partials in CTA order: results are bitwise reproducible for a fixed grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kry_device.cuh"
+
+namespace kry {
+
+struct SmemHead {
+    uint32_t koff[20];
+    uint32_t bsz[20];
+};
+
+// ---------------------------------------------------------------- y = H x
+
+template <class V>
+__global__ void __launch_bounds__(NTHR) k_apply(DevBasis b, DevHam hm, const V *__restrict__ x,
+                                                V *__restrict__ y, int rl_smem)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemHead *hd = (SmemHead *)smem;
+    uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHead));
+    stage_tables(b, hd->koff, hd->bsz, rl_s, rl_smem);
+    __syncthreads();
+    const uint16_t *rl = rl_smem ? rl_s : b.ranklo;
+    const uint32_t ntiles = (b.D + TILE - 1) / TILE;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TILE, t = threadIdx.x;
+        if (r0 + t < b.D) {
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(b, hd->bsz, r0, t, hi, off, klo);
+            y[r0 + t] = hv_row<V>(b, hm, x, hi, off, klo, hd->koff, rl);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Write this CTA's partials, then let the last CTA sum all partials (CTA order) into
+// fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).
+__device__ __forceinline__ bool finish_partials(const double2 *red, double2 *part, KryCtl *ctl,
+                                                double2 *fin, int *flag)
+{
+    const int tid = threadIdx.x;
+    if (tid < PSTRIDE) part[(size_t)blockIdx.x * PSTRIDE + tid] = red[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *flag = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!*flag) return false;
+    __threadfence();
+    if (tid < PSTRIDE) {
+        double2 s = make_double2(0.0, 0.0);
+        for (unsigned c = 0; c < gridDim.x; ++c) {
+            double2 v = __ldcg(part + (size_t)c * PSTRIDE + tid);
+            s.x += v.x;
+            s.y += v.y;
+        }
+        fin[tid] = s;
+    }
+    __syncthreads();
+    return true;
+}
+
+// Sum per-thread values over the CTA (warp shuffles, then warps in order) into red[slot].
+__device__ __forceinline__ void cta_sum_into(double2 v, double2 *red, int slot, double2 *wtmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) wtmp[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int w = 0; w < NTHR / 32; ++w) { s.x += wtmp[w].x; s.y += wtmp[w].y; }
+        red[slot] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- pass A
+
+template <class V>
+__global__ void __launch_bounds__(NTHR, 2) k_passA(EvArgs<V> a, int jj)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done || jj >= ctl->m_eff) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *utile = (V *)smem;
+    double2 *red = (double2 *)(smem + sizeof(V) * TILE);
+    double2 *wtmp = red + PSTRIDE;
+    SmemHead *hd = (SmemHead *)(wtmp + NTHR / 32);
+    int *flag = (int *)(hd + 1);
+    uint16_t *rl_s = (uint16_t *)(flag + 4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
+    __syncthreads();
+    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
+    const double sj = ctl->sigma[jj];
+    const V *x = a.W + (size_t)jj * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    DotAcc<V> acc[4];
+    DotAcc<V> nrm;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TILE;
+        V u = VT<V>::zero();
+        if (r0 + tid < D) {
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(a.b, hd->bsz, r0, tid, hi, off, klo);
+            u = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
+            a.U[r0 + tid] = u;
+            nrm.add(u, u);
+        }
+        utile[tid] = u;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iv = warp + 8 * q;
+            if (iv <= jj) {
+                const V *wi = a.W + (size_t)iv * a.ldW + r0;
+                V vv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t rr = lane + 32 * e;
+                    vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[q].add(vv[e], utile[lane + 32 * e]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int iv = warp + 8 * q;
+        double2 v = warp_sum(acc[q].value());
+        if (lane == 0 && iv <= jj) red[iv] = v;
+    }
+    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
+    double2 *fin = red;   // reused after the partials are written
+    if (!finish_partials(red, a.part, ctl, fin, flag)) return;
+    if (tid == 0) {
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i];
+            const double2 c = make_double2(fin[i].x * s, fin[i].y * s);   // <v_i, u>
+            ctl->coefA[i] = make_double2(c.x * s, c.y * s);
+            if (i == jj) ctl->alpha[jj] = c.x;
+        }
+        ctl->normu2 = fin[SLOT_NRM].x;
+        ctl->n_hv += 1;
+        ctl->vec_passes += (double)(jj + 2);
+        ctl->counter = 0;
+    }
+}
+
+// ---------------------------------------------------------------- linear combinations
+
+__device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, double2 gdot)
+{
+    const double bt = sqrt(nw2);
+    ctl->beta[jj] = bt;
+    if (!(bt > ctl->eta_bd * sqrt(ctl->normu2))) {   // invariant subspace (or zero vector)
+        ctl->m_eff = jj + 1;
+        ctl->n_bd += 1;
+    } else {
+        const double s = 1.0 / bt;
+        ctl->sigma[jj + 1] = s;
+        ctl->g[jj + 1] = make_double2(gdot.x * s, gdot.y * s);
+    }
+}
+
+template <class V, int MODE>
+__global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done) return;
+    if (MODE <= 1 && jj >= ctl->m_eff) return;
+    if (MODE == 1 && !ctl->corr) return;
+    const int nvec = (MODE == 2) ? ctl->m_eff : ((MODE == 3) ? 0 : jj + 1);
+    __shared__ V coef[MMAX + 1];
+    __shared__ V wtile[TILE];
+    __shared__ double2 red[PSTRIDE];
+    __shared__ double2 wtmp[NTHR / 32];
+    __shared__ int flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    if (tid < nvec) {
+        const double2 c = (MODE == 0) ? ctl->coefA[tid] : (MODE == 1) ? ctl->coefC[tid] : ctl->coefY[tid];
+        coef[tid] = VT<V>::from(c);
+    }
+    __syncthreads();
+    V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
+    const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
+    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    DotAcc<V> acc[4];
+    DotAcc<V> nrm, gacc;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TILE, r = r0 + tid;
+        V w = VT<V>::zero();
+        if (r < D) {
+            if (src) w = src[r];
+            if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
+#pragma unroll 8
+                for (int i = 0; i < nvec; ++i) w = cfms(coef[i], a.W[(size_t)i * a.ldW + r], w);
+            } else {
+#pragma unroll 8
+                for (int i = 0; i < nvec; ++i) w = cfms(coef[i], __ldg(a.W + (size_t)i * a.ldW + r), w);
+            }
+            out[r] = w;
+            nrm.add(w, w);
+            if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
+        }
+        if (MODE == 0) {
+            wtile[tid] = w;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int iv = warp + 8 * q;
+                if (iv <= jj) {
+                    const V *wi = a.W + (size_t)iv * a.ldW + r0;
+                    V vv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t rr = lane + 32 * e;
+                        vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[q].add(vv[e], wtile[lane + 32 * e]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (MODE == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iv = warp + 8 * q;
+            double2 v = warp_sum(acc[q].value());
+            if (lane == 0 && iv <= jj) red[iv] = v;
+        }
+    }
+    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
+    if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
+    double2 *fin = red;
+    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (tid != 0) return;
+    const double nw2 = fin[SLOT_NRM].x;
+    const double2 gdot = fin[SLOT_G];
+    if (MODE == 0) {
+        double nd2 = 0.0;
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i];
+            nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
+        }
+        if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
+        ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
+            ctl->corr = 1;
+            for (int i = 0; i <= jj; ++i) {
+                const double s = ctl->sigma[i];
+                ctl->coefC[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
+            }
+            ctl->alpha[jj] += fin[jj].x * ctl->sigma[jj];
+        } else {
+            ctl->corr = 0;
+            finalize_beta(ctl, jj, nw2, gdot);
+        }
+    } else if (MODE == 1) {
+        ctl->n_corr += 1;
+        ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        ctl->corr = 0;
+        finalize_beta(ctl, jj, nw2, gdot);
+    } else {
+        const double b0 = sqrt(nw2);
+        if (!(b0 > 0.0)) {
+            ctl->err = KRY_EINVAL;
+            ctl->done = 1;
+        } else {
+            ctl->beta0 = b0;
+            ctl->sigma[0] = 1.0 / b0;
+            ctl->g[0] = (MODE == 3) ? make_double2(b0, 0.0)
+                                    : make_double2(gdot.x / b0, gdot.y / b0);
+        }
+        ctl->vec_passes += (double)(nvec + 1) + ((a.G && MODE == 2) ? 1.0 : 0.0);
+        ctl->m_eff = ctl->m;
+        ctl->corr = 0;
+        if (MODE == 2 && ctl->finishing) ctl->done = 1;
+    }
+    ctl->counter = 0;
+}
+
+template <class V>
+__global__ void k_set_basis_state(V *W0, uint32_t r0)
+{
+    V one = VT<V>::zero();
+    one.x = 1;
+    W0[r0] = one;
+}
+
+// ---------------------------------------------------------------- launchers
+
+size_t apply_smem(const DevBasis &b, int rl_smem, int)
+{
+    return sizeof(SmemHead) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
+}
+
+size_t passA_smem(const DevBasis &b, int rl_smem, int c64)
+{
+    return (c64 ? sizeof(float2) : sizeof(double2)) * TILE + sizeof(double2) * (PSTRIDE + NTHR / 32) +
+           sizeof(SmemHead) + 16 + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
+}
+
+template <class K>
+static int prep_smem(K kernel, size_t smem)
+{
+    if (smem > 48 * 1024) KRY_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KRY_OK;
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y, int rl_smem,
+                 cudaStream_t s)
+{
+    const size_t smem = apply_smem(b, rl_smem, c64);
+    const uint32_t ntiles = (b.D + TILE - 1) / TILE;
+    int grid = (int)std::min<uint32_t>(ntiles, (uint32_t)sm_count() * 8u);
+    if (c64) {
+        if (int rc = prep_smem(k_apply<float2>, smem)) return rc;
+        k_apply<float2><<<grid, NTHR, smem, s>>>(b, h, (const float2 *)x, (float2 *)y, rl_smem);
+    } else {
+        if (int rc = prep_smem(k_apply<double2>, smem)) return rc;
+        k_apply<double2><<<grid, NTHR, smem, s>>>(b, h, (const double2 *)x, (double2 *)y, rl_smem);
+    }
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template <class V>
+int vector_grid(const DevBasis &b, int rl_smem)
+{
+    const int c64 = sizeof(V) == sizeof(float2);
+    const size_t smem = passA_smem(b, rl_smem, c64);
+    if (int rc = prep_smem(k_passA<V>, smem)) return -rc;
+    int occA = 0, occB = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_passA<V>, NTHR, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0>, NTHR, 0);
+    int occ = std::max(1, std::min(occA, occB));
+    const uint32_t ntiles = (b.D + TILE - 1) / TILE;
+    return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * occ)));
+}
+
+template <class V>
+int launch_passA(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+{
+    const size_t smem = passA_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2));
+    k_passA<V><<<grid, NTHR, smem, s>>>(a, jj);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template <class V>
+int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
+{
+    switch (mode) {
+    case 0: k_lincomb<V, 0><<<grid, NTHR, 0, s>>>(a, jj); break;
+    case 1: k_lincomb<V, 1><<<grid, NTHR, 0, s>>>(a, jj); break;
+    case 2: k_lincomb<V, 2><<<grid, NTHR, 0, s>>>(a, jj); break;
+    default: k_lincomb<V, 3><<<grid, NTHR, 0, s>>>(a, jj); break;
+    }
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s)
+{
+    if (c64) k_set_basis_state<float2><<<1, 1, 0, s>>>((float2 *)W0, r0);
+    else k_set_basis_state<double2><<<1, 1, 0, s>>>((double2 *)W0, r0);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template int vector_grid<double2>(const DevBasis &, int);
+template int vector_grid<float2>(const DevBasis &, int);
+template int launch_passA<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
+template int launch_passA<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
+template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t);
+template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t);
+
+}  // namespace kry

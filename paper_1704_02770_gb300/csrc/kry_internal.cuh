@@ -1,0 +1,144 @@
+// Internal declarations of the GB300 Krylov library (not installed; see include/kry.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <vector>
+
+#include "kry.h"
+
+namespace kry {
+
+constexpr int MMAX = 32;       // largest Krylov dimension m (one warp holds the small problem)
+constexpr int TILE = 256;      // consecutive ranks per CTA tile
+constexpr int NTHR = 256;      // threads per CTA of the vector kernels
+constexpr int PSTRIDE = 40;    // partial-sum slots per CTA: MMAX+1 dots, then extras
+constexpr int SLOT_NRM = 34;   // slot of a squared norm
+constexpr int SLOT_G = 35;     // slot of the readout dot <psi0, w>
+constexpr int KMAX = 128;      // largest Chebyshev degree of the small exponential
+constexpr double XMAX = 50.0;  // largest tau * r (half-width) handled in one step
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define KRY_CU(call)                                                 \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::kry::cuda_fail(e_, #call);   \
+    } while (0)
+
+// Rank/unrank tables of one sector, resident on the device.
+//   rank(s) = blk[s >> Llo] + ranklo[s & ((1 << Llo) - 1)]
+// blk[hi] is the first rank of the block of states whose upper Lhi bits equal hi (the
+// block holds C(Llo, N - popc(hi)) states, in the order of their lower bits); blk is
+// non-decreasing (entries of empty blocks repeat the next start), so the block of a rank
+// is found by binary search.  lolist lists the Llo-bit patterns grouped by popcount k,
+// each group ascending and starting at koff[k]; ranklo[lo] is lo's index in its group.
+struct DevBasis {
+    const uint32_t *blk;
+    const uint16_t *ranklo;
+    const uint16_t *lolist;
+    const uint32_t *koff;   // [Llo + 2]
+    const uint32_t *bsz;    // [Llo + 1], C(Llo, k)
+    int *err;               // device error flag of rank/unrank
+    int L, N, Llo, Lhi;
+    uint32_t D;
+};
+
+// Hamiltonian parameters for the matrix-free H.v.  The field energy
+// sum_i h_i (n_i - 1/2) of a state is ehlo[position of lo in lolist] + ehhi[hi].
+struct DevHam {
+    const double *ehlo_d, *ehhi_d;
+    const float *ehlo_f, *ehhi_f;
+    double cz;      // J Delta / 4
+    double halfJ;   // J / 2
+    int nbonds;     // bonds of the chain (L-1 open, L on a ring with L >= 3)
+    int pbc;        // ring bond (L-1, 0) present
+};
+
+// Device control block of one evolution: Lanczos coefficients of the current Krylov
+// step, time-stepping state and counters.  Written only by single-thread epilogues.
+struct KryCtl {
+    double alpha[MMAX + 1], beta[MMAX + 1], sigma[MMAX + 2];
+    double2 coefA[MMAX + 1];   // update coefficients c_i sigma_i of pass B
+    double2 coefC[MMAX + 1];   // correction coefficients of pass C
+    double2 coefY[MMAX + 1];   // combine coefficients -beta0 y_i sigma_i
+    double2 g[MMAX + 2];       // readout <psi0, v_i>
+    double normu2;             // ||H v_j||^2 of the last pass A
+    double beta0;              // ||psi|| at the start of the Krylov step
+    double t_now, t_end, tol, tau_prev;
+    double eta_corr, eta_bd;   // second-pass and breakdown thresholds (relative)
+    double err_sum, max_orth, vec_passes;
+    long long n_hv, n_steps, n_corr, n_bd;
+    int m, m_eff, corr, finishing, done, err;
+    int n_times, next_out, r0;
+    unsigned int counter;      // ticket of the last-CTA reductions
+};
+
+template <class V>
+struct EvArgs {
+    DevBasis b;
+    DevHam h;
+    V *W;            // Krylov vectors W_0..W_m, v_i = sigma_i W_i
+    size_t ldW;      // elements between consecutive W_i
+    V *U;            // H v_j
+    const V *G;      // readout vector psi0 (general initial state) or nullptr
+    double2 *part;   // per-CTA partial sums [grid][PSTRIDE]
+    KryCtl *ctl;
+    int rl_smem;     // stage ranklo in shared memory
+};
+
+struct ExpArgs {
+    KryCtl *ctl;
+    const double *times;
+    double *P;
+    const void *W;   // Krylov vectors (element type given by c64)
+    size_t ldW;
+    int c64;
+};
+
+size_t passA_smem(const DevBasis &b, int rl_smem, int c64);
+size_t lincomb_smem(int c64);
+size_t apply_smem(const DevBasis &b, int rl_smem, int c64);
+
+// kernel launchers (kry_hv.cu)
+int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y,
+                 int rl_smem, cudaStream_t s);
+template <class V> int launch_passA(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid,
+                                      cudaStream_t s);
+template <class V> int vector_grid(const DevBasis &b, int rl_smem);
+int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
+// small exponential (kry_exp.cu)
+int launch_smallexp(const ExpArgs &a, cudaStream_t s);
+
+}  // namespace kry
+
+struct kry_basis_s {
+    int L, N, Llo, Lhi;
+    int64_t D;
+    void *d_tab;
+    kry::DevBasis dev;
+    int device;
+};
+
+struct kry_ham_s {
+    kry_basis b;
+    double J, Delta;
+    int K, boundary;
+    std::vector<double> h;
+    void *d_eh;
+    kry::DevHam dev;
+    // evolution workspace (grown on demand, freed by kry_hamiltonian_destroy)
+    void *ws;
+    size_t ws_bytes;
+    // cached CUDA graph of one Krylov step
+    cudaGraphExec_t gexec;
+    int g_dtype, g_m, g_general, g_grid;
+    void *g_ws;
+    const void *g_G;
+    cudaStream_t cap_stream;
+    void *h_poll;   // pinned host mirror of the control block
+};

@@ -1,0 +1,210 @@
+"""GPU return probability / evolution against the oracle (the parity tests proper).
+
+Bars (from the workloads' accuracy targets): complex128 |P_gpu - P_oracle| <= 1e-10 at
+every output time; complex64 (mixed precision) <= 1e-5.  The oracle runs at tol = 1e-12,
+so its own error is far below either bar.  The measured error is printed for every case.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import basis as ob
+from oracle import dense, krylov
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_P(L, N, J, Delta, h, pbc, state, times, tol=1e-12):
+    H = ob.CSR(L, N, J, Delta, h, pbc)
+    P, _ = krylov.return_probability(H, ob.lookup(H.basis, state), times, m=30, tol=tol)
+    return P
+
+
+def _gpu_P(kry, L, N, J, Delta, h, pbc, state, times, m=30, tol=1e-10, dtype="c128"):
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, J, Delta, h, pbc=pbc)
+    return H.return_probability(state, times, m=m, tol=tol, dtype=dtype)
+
+
+def _report(name, err):
+    print(f"[parity] {name}: max|dP| = {err:.3e}")
+
+
+def test_config_L16_fp64(kry):
+    c = workloads.config("L16_fp64")
+    P, st = _gpu_P(kry, c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"], c["state"],
+                   c["times"], m=c["m"], tol=c["tol"])
+    Po = _oracle_P(c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"], c["state"], c["times"])
+    err = float(np.max(np.abs(P - Po)))
+    _report("L16 c128", err)
+    assert err <= 1e-10
+    assert st["n_krylov_steps"] > 10 and st["n_hv"] >= 30 * st["n_krylov_steps"] - 30
+    assert st["max_orth_loss"] < 1e-10
+
+
+def test_config_L16_mixed(kry):
+    c = workloads.config("L16_fp64")
+    P, st = _gpu_P(kry, c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"], c["state"],
+                   c["times"], m=c["m"], tol=1e-7, dtype="c64")
+    Po = _oracle_P(c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"], c["state"], c["times"])
+    err = float(np.max(np.abs(P - Po)))
+    _report("L16 c64", err)
+    assert err <= 1e-5
+
+
+@pytest.mark.parametrize("L,pbc,hh,Delta", [(10, True, 2.0, 1.0), (10, False, 1.0, 0.5),
+                                            (12, True, 0.0, 1.0), (13, True, 1.0, 0.3)])
+def test_small_sectors_vs_dense(kry, L, pbc, hh, Delta):
+    N = L // 2
+    h = workloads.quasiperiodic_field(L, hh, 0.4)
+    st = workloads.neel_state(L) if L % 2 == 0 else workloads.neel_state(L - 1)
+    times = workloads.log_times(40, 0.1, 100.0)
+    P, _ = _gpu_P(kry, L, N, 1.0, Delta, h, pbc, st, times)
+    b = dense.sector_states(L, N)
+    psi0 = np.zeros(b.size, complex)
+    psi0[int(np.searchsorted(b, st))] = 1.0
+    Pd = dense.return_probability_dense(dense.hamiltonian_kron(L, 1.0, Delta, h, pbc, N), psi0, times)
+    err = float(np.max(np.abs(P - Pd)))
+    _report(f"L{L} vs eigh", err)
+    assert err <= 1e-10
+
+
+def test_free_fermions(kry):
+    L, N = 14, 7
+    h = workloads.quasiperiodic_field(L, 1.0, 2.2)
+    times = workloads.log_times(20, 0.1, 50.0)
+    st = workloads.neel_state(L)
+    P, _ = _gpu_P(kry, L, N, 1.0, 0.0, h, True, st, times)
+    err = float(np.max(np.abs(P - dense.free_fermion_P(L, 1.0, h, True, st, times))))
+    _report("free fermions L14", err)
+    assert err <= 1e-10
+
+
+def test_edge_cases(kry):
+    times = [0.0, 0.0, 0.3, 1.0, 7.0, 30.0]
+    h4 = [0.3, -0.2, 0.5, 0.1]
+    # D = 6 < m: the Krylov space becomes invariant (breakdown)
+    P, st = _gpu_P(kry, 4, 2, 1.0, 0.5, h4, True, 0b0101, times)
+    assert np.max(np.abs(P - _oracle_P(4, 2, 1.0, 0.5, h4, True, 0b0101, times))) <= 1e-12
+    assert st["n_breakdowns"] >= 1
+    assert P[0] == pytest.approx(1.0, abs=1e-15) and P[1] == pytest.approx(1.0, abs=1e-15)
+    # empty and full sectors: P = 1
+    for N in (0, 6):
+        P, _ = _gpu_P(kry, 6, N, 1.0, 1.0, [0.1] * 6, True, (1 << N) - 1, times)
+        assert np.max(np.abs(P - 1.0)) <= 1e-13
+    # two-level system
+    tt = np.linspace(0.0, 20.0, 9)
+    P, _ = _gpu_P(kry, 2, 1, 1.3, 0.4, [0.8, -0.3], False, 0b01, tt)
+    assert np.max(np.abs(P - dense.two_level_P(1.3, [0.8, -0.3], tt))) <= 1e-11
+    # small Krylov dimension, loose tolerance
+    L = 10
+    hq = workloads.quasiperiodic_field(L, 1.0, 0.2)
+    tt = [0.05, 0.2, 0.5]
+    P, st = _gpu_P(kry, L, 5, 1.0, 1.0, hq, True, workloads.neel_state(L), tt, m=4, tol=1e-6)
+    err = np.max(np.abs(P - _oracle_P(L, 5, 1.0, 1.0, hq, True, workloads.neel_state(L), tt)))
+    assert err <= 1e-6 and st["n_krylov_steps"] > 3
+
+
+def test_general_initial_state_and_psi_out(kry):
+    L, N = 12, 6
+    h = workloads.quasiperiodic_field(L, 1.5, 2.0)
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, 1.0, 1.0, h, pbc=True)
+    rng = np.random.default_rng(3)
+    psi0 = rng.normal(size=B.dim) + 1j * rng.normal(size=B.dim)
+    psi0 /= np.linalg.norm(psi0)
+    times = [0.0, 0.5, 2.0, 7.5]
+    x = torch.from_numpy(psi0).cuda()
+    out = torch.empty_like(x)
+    P, _ = H.evolve(x, times, m=30, tol=1e-10, psi_out=out)
+    Hc = ob.CSR(L, N, 1.0, 1.0, h, True)
+    Po, psio, _ = krylov.evolve(Hc.matvec, Hc.norm_inf(), psi0, times, m=30, tol=1e-12)
+    assert np.max(np.abs(P - Po)) <= 1e-10
+    assert np.linalg.norm(out.cpu().numpy() - psio) <= 1e-10
+    # complex64 input
+    P64, _ = H.evolve(x.to(torch.complex64), times, m=30, tol=1e-7)
+    assert np.max(np.abs(P64 - Po)) <= 1e-5
+
+
+def test_unitarity_forward_backward(kry):
+    L, N = 14, 7
+    h = np.array(workloads.quasiperiodic_field(L, 2.0, 0.9))
+    B = kry.Basis(L, N)
+    Hf = kry.Hamiltonian(B, 1.0, 1.0, h)
+    Hb = kry.Hamiltonian(B, -1.0, 1.0, -h)   # -H: J -> -J at fixed Delta flips every term
+    rng = np.random.default_rng(5)
+    psi0 = rng.normal(size=B.dim) + 1j * rng.normal(size=B.dim)
+    psi0 /= np.linalg.norm(psi0)
+    x = torch.from_numpy(psi0).cuda()
+    mid, back = torch.empty_like(x), torch.empty_like(x)
+    Hf.evolve(x, [5.0], psi_out=mid)
+    Hb.evolve(mid, [5.0], psi_out=back)
+    assert abs(torch.linalg.vector_norm(mid).item() - 1.0) <= 1e-11
+    assert torch.linalg.vector_norm(back - x).item() <= 1e-10
+
+
+def test_deterministic(kry):
+    c = workloads.config("L16_fp64")
+    a, _ = _gpu_P(kry, c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], c["times"][:20])
+    b, _ = _gpu_P(kry, c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], c["times"][:20])
+    assert np.array_equal(a, b)
+
+
+def test_unreachable_tolerance_reports_etol(kry):
+    with pytest.raises(kry.KryError) as e:
+        _gpu_P(kry, 10, 5, 1.0, 1.0, [0.5] * 10, True, workloads.neel_state(10), [1.0, 5.0], tol=1e-300)
+    assert e.value.code == kry.KRY_ETOL
+
+
+def test_bad_state_is_rejected(kry):
+    B = kry.Basis(10, 5)
+    H = kry.Hamiltonian(B, 1.0, 1.0, [0.0] * 10)
+    with pytest.raises(kry.KryError):
+        H.return_probability(0b111, [1.0])
+    with pytest.raises(kry.KryError):
+        H.return_probability(workloads.neel_state(10), [2.0, 1.0])
+
+
+@pytest.mark.parametrize("dtype,bar", [("c128", 1e-10), ("c64", 1e-5)])
+def test_config_L24_full_size(kry, dtype, bar):
+    """Full-size L=24 sector: the first output times against the oracle; all 40 checked
+    for range and against the other precision."""
+    c = workloads.config("L24_mixed")
+    times = c["times"]
+    P, st = _gpu_P(kry, c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], times,
+                   tol=c["tol"] if dtype == "c128" else 1e-7, dtype=dtype)
+    assert np.all(P >= -1e-12) and np.all(P <= 1.0 + 1e-12)
+    k = 6
+    Po = _oracle_P(c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], times[:k])
+    err = float(np.max(np.abs(P[:k] - Po)))
+    _report(f"L24 {dtype} (t <= {times[k - 1]:.3f})", err)
+    assert err <= bar
+
+
+def test_config_L24_mixed_vs_fp64(kry):
+    c = workloads.config("L24_mixed")
+    args = (kry, c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], c["times"])
+    P128, _ = _gpu_P(*args, tol=1e-10, dtype="c128")
+    P64, _ = _gpu_P(*args, tol=1e-7, dtype="c64")
+    err = float(np.max(np.abs(P128 - P64)))
+    _report("L24 c64 vs c128, 40 times to t=100", err)
+    assert err <= 1e-5
+
+
+def test_config_L30_full_size(kry):
+    """Full-size L=30 sector: short-time law P = 1 - (L J^2/4) t^2 + O(t^4) for the Neel
+    state on a ring, and complex64 against complex128 over the early output times."""
+    c = workloads.config("L30_qp")
+    L, N = c["L"], c["n_up"]
+    tt = [1e-3, 2e-3]
+    P, _ = _gpu_P(kry, L, N, 1.0, 1.0, c["h"][0], True, c["state"], tt, tol=1e-10, dtype="c128")
+    for t, p in zip(tt, P):
+        assert abs((1.0 - p) / t**2 - L / 4.0) < 1e-3 * L
+    times = c["times"][:10]
+    P128, st = _gpu_P(kry, L, N, 1.0, 1.0, c["h"][0], True, c["state"], times, tol=1e-10, dtype="c128")
+    torch.cuda.empty_cache()
+    P64, _ = _gpu_P(kry, L, N, 1.0, 1.0, c["h"][0], True, c["state"], times, tol=1e-7, dtype="c64")
+    err = float(np.max(np.abs(P128 - P64)))
+    _report("L30 c64 vs c128 (t <= 0.5)", err)
+    assert err <= 1e-5
