@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Krylov return-probability benchmark on one GB300 (replicas on N GPUs).
+
+Workload: the L = 24, N_up = 12 sector (D = 2,704,156) of the quasiperiodic XXZ chain
+(J = 1, Delta = 1, h = 1.5, phi from seed 2), Neel initial state, Krylov m = 30,
+P(t) at 40 log-spaced times in [0.1, 100], tol = 1e-10.  One step = one full evolution
+to t = 100 through kry_return_probability.  Metric: H.v state-updates per second
+(D x number of H.v applications / time), FP64 (complex128) form; the mixed-precision
+(complex64 vectors, FP64 coefficients) form is timed beside it with its error.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Krylov H.v state-updates/s (+ % HBM roofline), FP64 vs FP32/batched at set error"
+WORKLOAD = "L24_mixed"
+HBM_PEAK_FALLBACK = 6800.0
+KIND_NAMES = ("passA", "passB", "passC", "smallexp", "combine")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="FP64 timed region only (no mixed, e2e or CPU legs): for ncu captures")
+    a = ap.parse_args()
+    if a.kernels_only:
+        a.no_mixed = a.no_cpu_baseline = True
+    return a
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+# ---------------------------------------------------------------- clocks during the run
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.rows, self.proc, self.thr = index, [], None, None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+        self.thr = threading.Thread(target=reader, daemon=True)
+        self.thr.start()
+        return self
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thr:
+            self.thr.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 7
+                          for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def aggregate(units: float, seconds: float, world: int):
+    """Whole-job throughput of independent replicas: sum of units / max of times."""
+    if world == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- traffic from ncu
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kry_hv.cu", "kry_device.cuh", "kry_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1704_02770_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, if the kernel
+    sources still hash to the value recorded there; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic_L24.txt")
+    try:
+        rows = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
+    except OSError:
+        return None
+    if rows.get("source_hash") != kernel_source_hash():
+        return None
+    v = rows.get(f"{kind}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1704_02770_gb300 as kry
+    import workloads
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    kry.load()
+    c = workloads.config(args.workload)
+    L, N, times = c["L"], c["n_up"], c["times"]
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
+    D = B.dim
+    stream = torch.cuda.current_stream()
+
+    def evolve(dtype, tol):
+        return H.return_probability(c["state"], times, m=c["m"], tol=tol, dtype=dtype)
+
+    def timed(dtype, tol, profile):
+        for _ in range(args.warmup):
+            evolve(dtype, tol)
+        if profile:
+            H.profile(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hv = launches = 0
+        P = None
+        e0.record(stream)
+        for _ in range(args.steps):
+            P, st = evolve(dtype, tol)
+            hv += st["n_hv"]
+            launches += st["n_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        prof = H.profile_read() if profile else None
+        H.profile(False)
+        return e0.elapsed_time(e1) / 1e3, hv, launches, P, st, prof
+
+    clk = ClockSampler(local).start()
+    sec, hv, launches, P128, st128, prof = timed("c128", c["tol"], profile=True)
+    clocks = clk.stop()
+    units, sec_all = aggregate(D * hv, sec, world)
+    value = units / sec_all
+    out = {"metric": METRIC, "value": value, "unit": "state-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sec_all / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
+           "data": "synthetic (seeded quasiperiodic field, Neel state)"}
+    cfg = {"workload": f"{args.workload}: L={L} N_up={N} D={D} PBC J=1 Delta=1 h=1.5 "
+                       f"m={c['m']} tol={c['tol']:g} 40 log times in [0.1,100]",
+           "krylov_steps_per_step": st128["n_krylov_steps"], "hv_per_step": st128["n_hv"],
+           "second_passes_per_step": st128["n_second_pass"],
+           "parallelism": f"replicas x{world}",
+           "l2": "no flush: each step sweeps a 1.4 GB Krylov basis (31 vectors x 43 MB) > 129 MB L2"}
+    # roofline of the dominant kernel kind, from CUDA events inside the timed region
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
+    dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
+    per = {k: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / (v["ms"] * 1e6)) if v["ms"] else None,
+               "launches": v["launches"]} for k, v in prof.items()}
+    ach = prof[dom]["bytes"] / (prof[dom]["ms"] * 1e6)
+    tr = ncu_traffic(dom)
+    nl = max(prof[dom]["launches"], 1)
+    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
+                       "unit": "GB/s", "frac": ach / peak,
+                       "peak_source": "measured" if peaks else "fallback",
+                       "traffic": tr,
+                       "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
+                       "per_kind": per,
+                       "kernel_time_share": {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values())
+                                             for k in KIND_NAMES}}
+    out["gpu_launches"] = launches
+    out["clocks"] = clocks
+    # mixed precision at the same stated accuracy target
+    if not args.no_mixed:
+        sec64, hv64, l64, P64, st64, _ = timed("c64", 1e-7, profile=False)
+        u64, s64 = aggregate(D * hv64, sec64, world)
+        out["mixed"] = {"dtype": "c64 vectors, fp64 coefficients", "value": u64 / s64,
+                        "unit": "state-updates/s", "ms_per_step": 1e3 * s64 / args.steps,
+                        "speedup_vs_fp64": (u64 / s64) / value,
+                        "max_abs_dP_vs_fp64": float(np.max(np.abs(P64 - P128)))}
+        out["gpu_launches"] += l64
+    out["config"] = cfg
+    if args.kernels_only:
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    # end to end through the public API with host buffers: psi0 from pinned memory every step
+    psi_host = torch.zeros(D, dtype=torch.complex128).pin_memory()
+    r0 = B.rank(torch.tensor([c["state"]], dtype=torch.int64, device="cuda")).item()
+    psi_host[r0] = 1.0
+    x = torch.empty(D, dtype=torch.complex128, device="cuda")
+    for _ in range(max(1, args.warmup // 2)):
+        x.copy_(psi_host, non_blocking=True)
+        H.evolve(x, times, m=c["m"], tol=c["tol"])
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hv_e = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(psi_host, non_blocking=True)
+        Pe, ste = H.evolve(x, times, m=c["m"], tol=c["tol"])
+        hv_e += ste["n_hv"]
+        out["gpu_launches"] += ste["n_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ue, se = aggregate(D * hv_e, e0.elapsed_time(e1) / 1e3, world)
+    out["e2e"] = {"value": ue / se, "unit": "state-updates/s",
+                  "h2d_bytes_per_step": D * 16, "d2h_bytes_per_step": len(times) * 8,
+                  "api": "Hamiltonian.evolve (kry_evolve) on a psi0 copied from pinned host memory",
+                  "max_abs_dP_vs_basis_state_call": float(np.max(np.abs(Pe - P128)))}
+    out["config"] = cfg
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, cores=1)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(workload: str):
+    """One Krylov step (m = 30 Arnoldi with CGS2 and one Pade exponential) of the workload
+    with the CPU oracle, as it stands.  Returns (state-updates, seconds, D)."""
+    import numpy as np
+
+    from oracle import basis as ob
+    from oracle import krylov, pade
+    import workloads
+
+    c = workloads.config(workload)
+    H = ob.CSR(c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"])
+    psi = krylov.basis_vector(H.D, ob.lookup(H.basis, c["state"]))
+    t0 = time.perf_counter()
+    V, Hb, me = krylov.arnoldi_cgs2(H.matvec, psi, c["m"], H.norm_inf())
+    A = np.zeros((me + 1, me + 1), complex)
+    A[:me, :me] = -1j * 0.5 * Hb[:me, :me]
+    A[me, me - 1] = -1j * 0.5 * Hb[me, me - 1]
+    E = pade.expm(A)
+    _ = E[:me, 0] @ V[:me]
+    sec = time.perf_counter() - t0
+    return H.D * me, sec, H.D
+
+
+def cpu_baseline(workload: str, cores: int = 1):
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores))
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "u,s,D=bench.oracle_sample(%r); print(json.dumps([u,s,D]))" % (ROOT, workload))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    u, s, D = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": u / s, "unit": "state-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"one Krylov step (m=30 Arnoldi+CGS2, Pade exp) of {workload}, D={D}, "
+                      f"{s:.1f} s on {cores} host thread(s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"   # before numpy loads: the oracle runs on one host thread
+    samples = []
+    for i in range(args.warmup + args.steps):
+        u, s, D = oracle_sample(args.workload)
+        if i >= args.warmup:
+            samples.append((u, s))
+    units = sum(u for u, _ in samples)
+    sec = sum(s for _, s in samples)
+    v = units / sec
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "state-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / max(len(samples), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+        "data": "synthetic (seeded quasiperiodic field, Neel state)",
+        "config": {"workload": args.workload,
+                   "step": "one Krylov step (m=30) of the CPU oracle, a bounded sample"},
+        "cpu_baseline": {"value": v, "unit": "state-updates/s", "kind": "oracle",
+                         "cores": 1,
+                         "sample": "one Krylov step (m=30 Arnoldi+CGS2, Pade exp) per step"},
+        "e2e": {"value": v, "unit": "state-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

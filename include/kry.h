@@ -63,6 +63,7 @@ typedef struct kry_stats {
     double max_orth_loss;    /* max |<v_i, v_j>| / ||v_j|| seen before the correction        */
     double time_ms;          /* device time of the call (CUDA events)                        */
     double algo_bytes;       /* algorithmic HBM bytes of the call, by formula                 */
+    int64_t n_launches;      /* kernels the call launched (including no-op launches)          */
 } kry_stats;
 
 /* ---------------------------------------------------------------- basis (Sec. 2, Alg. 2)
@@ -125,6 +126,20 @@ int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const doub
  * the centre of T's Gershgorin interval.  1 <= m <= 32.  Synchronises `stream`. */
 int kry_tridiag_expv(const double *alpha, const double *beta, int m, double h, double tau,
                      double *y_out, double *err_out, void *stream);
+
+/* Per-kernel profile (not part of the paper's method; a measurement aid).
+ * kry_profile_enable(H, 1) makes later kry_evolve / kry_return_probability calls on H
+ * record CUDA events between the kernels of every Krylov step (on the caller's stream,
+ * inside the replayed graph) and synchronise after each step; 0 turns it off.
+ * kry_profile_read fills, for the five kernel kinds
+ *   0 = pass A (H.v fused with the reorthogonalisation dots), 1 = pass B (Lanczos update
+ *   with the second-pass dots), 2 = pass C (second-pass correction), 3 = small
+ *   exponential and step control, 4 = combine psi = beta V y,
+ * the summed event time in ms, the algorithmic HBM bytes (vector reads and writes by
+ * formula; gathers of H.v beyond one read of v_j are not counted) and the launch count,
+ * accumulated since the last kry_profile_enable(H, 1).  Arrays have 5 entries, host. */
+int kry_profile_enable(kry_ham H, int on);
+int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
 
 /* Bytes of device workspace kry_evolve allocates for (H, dtype, m); -1 on bad input. */
 int64_t kry_workspace_size(kry_ham H, int dtype, int m);

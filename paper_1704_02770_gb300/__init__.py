@@ -27,7 +27,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n_hv", ctypes.c_int64), ("n_krylov_steps", ctypes.c_int64),
                 ("n_second_pass", ctypes.c_int64), ("n_breakdowns", ctypes.c_int64),
                 ("err_estimate", ctypes.c_double), ("max_orth_loss", ctypes.c_double),
-                ("time_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double)]
+                ("time_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double),
+                ("n_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -47,6 +48,8 @@ SIGNATURES = {
                                     ctypes.POINTER(Stats), _vp]),
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_workspace_size": (_i64, [_vp, _i, _i]),
+    "kry_profile_enable": (_i, [_vp, _i]),
+    "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "kry_last_error": (ctypes.c_char_p, []),
 }
 
@@ -187,6 +190,20 @@ class Hamiltonian:
         _check(load().kry_return_probability(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                              P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
+
+    def profile(self, on: bool = True):
+        """Turn per-kernel CUDA-event profiling of later evolutions on or off (resets it)."""
+        _check(load().kry_profile_enable(self._h, 1 if on else 0))
+
+    KINDS = ("passA", "passB", "passC", "smallexp", "combine")
+
+    def profile_read(self):
+        import numpy as np
+        ms, by = np.zeros(5), np.zeros(5)
+        n = (ctypes.c_int64 * 5)()
+        _check(load().kry_profile_read(self._h, ms.ctypes.data_as(_dp), by.ctypes.data_as(_dp), n))
+        return {k: dict(ms=float(ms[i]), bytes=float(by[i]), launches=int(n[i]))
+                for i, k in enumerate(self.KINDS)}
 
     def workspace_size(self, dtype: str = "c128", m: int = 30) -> int:
         return int(load().kry_workspace_size(self._h, KRY_C64 if dtype == "c64" else KRY_C128, m))

@@ -67,6 +67,15 @@ void drop_graph(kry_ham_s *H)
 {
     if (H->gexec) cudaGraphExecDestroy(H->gexec);
     H->gexec = nullptr;
+    for (cudaEvent_t e : H->prof_ev) cudaEventDestroy(e);
+    H->prof_ev.clear();
+}
+
+// kernel kind of the k-th launch in the captured step (3 per Lanczos index, then 2)
+int kind_of(int k, int m)
+{
+    if (k < 3 * m) return k % 3;   // pass A, pass B, pass C
+    return k == 3 * m ? KIND_EXP : KIND_COMBINE;
 }
 
 template <class V>
@@ -74,15 +83,33 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
+    const int nk = 3 * m + 2;   // kernels per step
+    if (H->prof_on) {
+        H->prof_ev.resize(nk + 1);
+        for (auto &e : H->prof_ev) KRY_CU(cudaEventCreate(&e));
+    }
     KRY_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    int rc = KRY_OK;
+    int rc = KRY_OK, k = 0;
+    auto mark = [&]() {
+        if (H->prof_on && rc == KRY_OK) {
+            cudaError_t er = cudaEventRecord(H->prof_ev[k], cs);
+            if (er != cudaSuccess) rc = cuda_fail(er, "cudaEventRecord(capture)");
+        }
+        ++k;
+    };
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
+        mark();
         rc = launch_passA<V>(a, jj, grid, cs);
+        mark();
         if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, grid, cs);
+        mark();
         if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, grid, cs);
     }
+    mark();
     if (rc == KRY_OK) rc = launch_smallexp(ea, cs);
+    mark();
     if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, grid, cs);
+    mark();
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -133,7 +160,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
                      H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
-                     H->ws_bytes < l.bytes))
+                     H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on))
         drop_graph(H);
     if (!H->gexec) {
         if (int rc = capture_step<V>(H, a, ea, m, grid)) return rc;
@@ -181,11 +208,22 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     long long launched = 0;
     const long long max_launch = 500000;   // Krylov steps before KRY_ETIMEOUT
     int batch = 1;
+    const int nk = 3 * m + 2;
+    const double vp0[5] = {0, 0, 0, 0, 0};
     for (;;) {
+        if (H->prof_on) batch = 1;   // events are read after every step
         for (int i = 0; i < batch; ++i) KRY_CU(cudaGraphLaunch(H->gexec, s));
         launched += batch;
         KRY_CU(cudaMemcpyAsync(hp, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, s));
         KRY_CU(cudaStreamSynchronize(s));
+        if (H->prof_on) {
+            for (int k = 0; k < nk; ++k) {
+                float ms = 0.f;
+                KRY_CU(cudaEventElapsedTime(&ms, H->prof_ev[k], H->prof_ev[k + 1]));
+                H->prof_ms[kind_of(k, m)] += ms;
+                H->prof_launches[kind_of(k, m)] += 1;
+            }
+        }
         if (hp->done) break;
         if (launched >= max_launch) {
             set_error("kry_evolve: no convergence after %lld Krylov steps (t = %g of %g)", launched,
@@ -197,6 +235,9 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         batch = (int)std::min(64.0, std::max(1.0, std::ceil(est * 1.05)));
     }
     KRY_CU(cudaEventRecord(ev1, s));
+    if (H->prof_on)
+        for (int q = 0; q < NKIND; ++q)
+            H->prof_bytes[q] += (hp->vp_kind[q] - vp0[q]) * (double)nvec * (double)es;
     if (hp->err) {
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
@@ -220,6 +261,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
+        st->n_launches = launched * nk + (general ? 1 : 1);
     }
     return KRY_OK;
 }
@@ -252,6 +294,21 @@ extern "C" int kry_hamiltonian_destroy(kry_ham H)
     if (H->h_poll) cudaFreeHost(H->h_poll);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     delete H;
+    return KRY_OK;
+}
+
+extern "C" int kry_profile_enable(kry_ham H, int on)
+{
+    if (!H) { set_error("kry_profile_enable: H is NULL"); return KRY_EINVAL; }
+    H->prof_on = on ? 1 : 0;
+    for (int q = 0; q < NKIND; ++q) { H->prof_ms[q] = 0.0; H->prof_bytes[q] = 0.0; H->prof_launches[q] = 0; }
+    return KRY_OK;
+}
+
+extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches)
+{
+    if (!H || !ms || !bytes || !launches) { set_error("kry_profile_read: bad arguments"); return KRY_EINVAL; }
+    for (int q = 0; q < NKIND; ++q) { ms[q] = H->prof_ms[q]; bytes[q] = H->prof_bytes[q]; launches[q] = H->prof_launches[q]; }
     return KRY_OK;
 }
 

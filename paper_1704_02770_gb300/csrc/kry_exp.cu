@@ -216,8 +216,10 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
             const double2 s = integral_sum(myJ, sm.tch + (me - 1), 32, K);
             eq = beta0 * fabs(h) / r * sqrt(s.x * s.x + s.y * s.y);
         }
-        const bool ok = (tq > 0.0 || remaining <= 0.0) &&
-                        eq <= STEP_SAFETY * 0.5 * tol * tq / t_end;
+        // a step's error budget must stay above the FP64 rounding unit of psi, otherwise
+        // the tolerance is unreachable (KRY_ETOL) rather than met by ever smaller steps
+        const double budget = STEP_SAFETY * 0.5 * tol * tq / t_end;
+        const bool ok = tq > 0.0 && budget >= 2.3e-16 * beta0 && eq <= budget;
         const unsigned mask = __ballot_sync(0xffffffffu, ok || (remaining <= 0.0));
         if (mask) {
             pick = __ffs(mask) - 1;

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_passA(EvArgs<V> a, int jj)
         ctl->normu2 = fin[SLOT_NRM].x;
         ctl->n_hv += 1;
         ctl->vec_passes += (double)(jj + 2);
+        ctl->vp_kind[0] += (double)(jj + 2);
         ctl->counter = 0;
     }
 }
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
         }
         if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        ctl->vp_kind[1] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
             ctl->corr = 1;
             for (int i = 0; i <= jj; ++i) {
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
     } else if (MODE == 1) {
         ctl->n_corr += 1;
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        ctl->vp_kind[2] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         ctl->corr = 0;
         finalize_beta(ctl, jj, nw2, gdot);
     } else {
@@ -293,6 +296,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
                                     : make_double2(gdot.x / b0, gdot.y / b0);
         }
         ctl->vec_passes += (double)(nvec + 1) + ((a.G && MODE == 2) ? 1.0 : 0.0);
+        if (MODE == 2) ctl->vp_kind[4] += (double)(nvec + 1) + (a.G ? 1.0 : 0.0);
         ctl->m_eff = ctl->m;
         ctl->corr = 0;
         if (MODE == 2 && ctl->finishing) ctl->done = 1;

@@ -71,6 +71,7 @@ struct KryCtl {
     double t_now, t_end, tol, tau_prev;
     double eta_corr, eta_bd;   // second-pass and breakdown thresholds (relative)
     double err_sum, max_orth, vec_passes;
+    double vp_kind[5];         // vector passes by kernel kind (pass A, B, C, -, combine)
     long long n_hv, n_steps, n_corr, n_bd;
     int m, m_eff, corr, finishing, done, err;
     int n_times, next_out, r0;
@@ -114,6 +115,9 @@ int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
 // small exponential (kry_exp.cu)
 int launch_smallexp(const ExpArgs &a, cudaStream_t s);
 
+// kernel kinds of the profile
+enum { KIND_PASSA = 0, KIND_PASSB = 1, KIND_PASSC = 2, KIND_EXP = 3, KIND_COMBINE = 4, NKIND = 5 };
+
 }  // namespace kry
 
 struct kry_basis_s {
@@ -141,4 +145,9 @@ struct kry_ham_s {
     const void *g_G;
     cudaStream_t cap_stream;
     void *h_poll;   // pinned host mirror of the control block
+    // profiling: CUDA events recorded between the kernels of the captured step
+    int prof_on;
+    std::vector<cudaEvent_t> prof_ev;
+    double prof_ms[5], prof_bytes[5];
+    int64_t prof_launches[5];
 };
