@@ -141,18 +141,39 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind):
-    """DRAM bytes per launch of `kind` from the committed ncu summary, if the kernel
-    sources still hash to the value recorded there; else None."""
+def ncu_traffic(kind, algo_bytes_per_launch):
+    """DRAM bytes per (average) launch of `kind`: the committed ncu capture of one launch,
+    scaled by algorithmic bytes to the average launch; None if the kernel sources no
+    longer hash to the value recorded with the capture."""
     path = os.path.join(ROOT, "profiles", "traffic_L24.txt")
     try:
-        rows = dict(line.strip().split("=", 1) for line in open(path) if "=" in line)
+        rows = dict(line.strip().split("=", 1) for line in open(path)
+                    if "=" in line and not line.startswith("#"))
     except OSError:
         return None
     if rows.get("source_hash") != kernel_source_hash():
         return None
-    v = rows.get(f"{kind}_dram_bytes_per_launch")
-    return float(v) if v else None
+    dram, algo = rows.get(f"{kind}_captured_dram_bytes"), rows.get(f"{kind}_captured_algo_bytes")
+    if not dram or not algo:
+        return None
+    return float(dram) / float(algo) * algo_bytes_per_launch
+
+
+def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
+    """Algorithmic FP64 flops of all launches of `kind` over `krylov_steps` full steps.
+
+    Per element: a complex multiply-add is 8 flops, |w|^2 is 4.  Pass A at Lanczos index j
+    does the H.v row (2 flops per gathered neighbour, 10 for the diagonal term and the
+    J/2 scale) and j+1 dots; pass B does j+1 updates and j+1 second-pass dots.
+    The average number of neighbours is 2N(L-N)/(L-1) on a ring, 2N(L-N)/L open."""
+    nb = 2.0 * N * (L - N) / ((L - 1) if pbc else L)
+    if kind == "passA":
+        per = sum(8 * (j + 1) + 4 + 10 + 2 * nb for j in range(m))
+    elif kind == "passB":
+        per = sum(16 * (j + 1) + 4 for j in range(m))
+    else:
+        return 0.0
+    return per * D * krylov_steps
 
 
 # ---------------------------------------------------------------- our arm
@@ -225,13 +246,22 @@ def run_ours(args):
     per = {k: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / (v["ms"] * 1e6)) if v["ms"] else None,
                "launches": v["launches"]} for k, v in prof.items()}
     ach = prof[dom]["bytes"] / (prof[dom]["ms"] * 1e6)
-    tr = ncu_traffic(dom)
     nl = max(prof[dom]["launches"], 1)
-    out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak,
-                       "unit": "GB/s", "frac": ach / peak,
-                       "peak_source": "measured" if peaks else "fallback",
+    tr = ncu_traffic(dom, prof[dom]["bytes"] / nl)
+    # The complex128 kernels issue FP64 arithmetic on every vector element; on GB300 the
+    # FP64 pipe (4 flop/clk/SM) saturates before HBM does, so their bound is the ALU.
+    fl = fp64_flops(dom, D, c["m"], hv // c["m"], L, N, c["pbc"])
+    mhz = clocks["sm_mhz"] or 2070.0
+    fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
+    ach_fl = fl / (prof[dom]["ms"] * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
+                       "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
+                       "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
                        "traffic": tr,
                        "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
+                       "hbm_view": {"achieved": ach, "peak": peak, "unit": "GB/s",
+                                    "frac": ach / peak,
+                                    "peak_source": "measured" if peaks else "fallback"},
                        "per_kind": per,
                        "kernel_time_share": {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values())
                                              for k in KIND_NAMES}}

@@ -92,7 +92,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     int rc = KRY_OK, k = 0;
     auto mark = [&]() {
         if (H->prof_on && rc == KRY_OK) {
-            cudaError_t er = cudaEventRecord(H->prof_ev[k], cs);
+            cudaError_t er = cudaEventRecordWithFlags(H->prof_ev[k], cs, cudaEventRecordExternal);
             if (er != cudaSuccess) rc = cuda_fail(er, "cudaEventRecord(capture)");
         }
         ++k;

@@ -151,6 +151,28 @@ def test_deterministic(kry):
     assert np.array_equal(a, b)
 
 
+def test_profiling_changes_nothing_and_counts_every_kernel(kry):
+    c = workloads.config("L16_fp64")
+    B = kry.Basis(c["L"], c["n_up"])
+    H = kry.Hamiltonian(B, 1.0, 1.0, c["h"][0])
+    P0, st0 = H.return_probability(c["state"], c["times"][:25], tol=1e-10)
+    H.profile(True)
+    P1, st1 = H.return_probability(c["state"], c["times"][:25], tol=1e-10)
+    prof = H.profile_read()
+    H.profile(False)
+    assert np.array_equal(P0, P1)
+    m = 30
+    steps = prof["smallexp"]["launches"]
+    assert steps >= st1["n_krylov_steps"]
+    for k in ("passA", "passB", "passC"):
+        assert prof[k]["launches"] == m * steps and prof[k]["ms"] > 0.0
+    assert prof["combine"]["launches"] == steps
+    # algorithmic bytes of pass A: sum over j of (j + 2) vectors of D complex128
+    want = st1["n_krylov_steps"] * sum(j + 2 for j in range(m)) * B.dim * 16
+    assert prof["passA"]["bytes"] == pytest.approx(want, rel=1e-12)
+    assert st1["n_launches"] == steps * (3 * m + 2) + 1
+
+
 def test_unreachable_tolerance_reports_etol(kry):
     with pytest.raises(kry.KryError) as e:
         _gpu_P(kry, 10, 5, 1.0, 1.0, [0.5] * 10, True, workloads.neel_state(10), [1.0, 5.0], tol=1e-300)
