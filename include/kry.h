@@ -127,6 +127,23 @@ int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const doub
 int kry_tridiag_expv(const double *alpha, const double *beta, int m, double h, double tau,
                      double *y_out, double *err_out, void *stream);
 
+/* The paper has no counterpart to this call: it is kry_tridiag_expv for callers that must
+ * not allocate device memory.  Some callers give every byte of device memory to their own
+ * pool with a hard limit, so an extra cudaMalloc can fail.  Others cannot let cudaFree
+ * synchronise the whole device while their other streams are running.  kry_tridiag_expv
+ * does a cudaMalloc and a cudaFree on every call; this variant calls neither, nor any
+ * other routine that allocates.  Arguments and results are those of kry_tridiag_expv.
+ * Its device scratch is one fixed array of about 1 KB, which every GPU that loads the
+ * library keeps until the process exits.  That array caps m at 32; a larger m returns
+ * KRY_EINVAL with a message naming the limit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current) and keeps it;
+ * make that first call before any stream capture.  All calls share the one array: calls
+ * whose GPU work overlaps (two host threads, or two streams) race on it and must be
+ * serialised by the caller.  Each call copies in every value its kernel reads, so nothing
+ * left in the array by an earlier call affects the result.  Synchronises `stream`. */
+int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, double h,
+                             double tau, double *y_out, double *err_out, void *stream);
+
 /* Per-kernel profile (not part of the paper's method; a measurement aid).
  * kry_profile_enable(H, 1) makes later kry_evolve / kry_return_probability calls on H
  * record CUDA events between the kernels of every Krylov step (on the caller's stream,

@@ -47,6 +47,7 @@ SIGNATURES = {
     "kry_return_probability": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp,
                                     ctypes.POINTER(Stats), _vp]),
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
+    "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_workspace_size": (_i64, [_vp, _i, _i]),
     "kry_profile_enable": (_i, [_vp, _i]),
     "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),

@@ -376,3 +376,83 @@ extern "C" int kry_tridiag_expv(const double *alpha, const double *beta, int m, 
     if (e != cudaSuccess) return cuda_fail(e, "kry_tridiag_expv");
     return KRY_OK;
 }
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// kry_tridiag_expv_noalloc runs the same kernel as kry_tridiag_expv, but its device-side
+// copies of alpha, beta and the results live in the fixed array below instead of memory
+// from cudaMalloc.  It serves callers that hand all device memory to their own pool with a
+// hard cap, and callers that cannot accept the device-wide synchronisation that cudaFree
+// performs while their other streams are busy.
+//
+// The array holds alpha[32], beta[32], y[64] and err (about 1 KB).  Every GPU that loads
+// this library keeps it for the life of the process.  Host code cannot pass the array's
+// name to a kernel (in host code it is a stand-in, not a device address), so the first
+// call on each device looks up the real address with cudaGetSymbolAddress while that
+// device is current and caches it.
+
+#include <mutex>
+
+static __device__ __align__(256) double g_expv_scratch[4 * kry::MMAX + 8];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_expv_mu;
+double *g_expv_addr[kMaxDevices] = {};
+
+int expv_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("kry_tridiag_expv_noalloc: device ordinal %d is above %d", dev, kMaxDevices - 1);
+        return KRY_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_expv_mu);
+    if (!g_expv_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_expv_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_expv_scratch)");
+        g_expv_addr[dev] = (double *)p;
+    }
+    *out = g_expv_addr[dev];
+    return KRY_OK;
+}
+}  // namespace
+
+extern "C" int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, double h,
+                                        double tau, double *y_out, double *err_out, void *stream)
+{
+    if (m > MMAX) {
+        set_error("kry_tridiag_expv_noalloc: m = %d exceeds the maximum %d that its fixed "
+                  "device scratch holds", m, MMAX);
+        return KRY_EINVAL;
+    }
+    if (!alpha || (m > 1 && !beta) || !y_out || !err_out || m < 1 || !(tau >= 0.0) ||
+        !(tau < 1e300)) {
+        set_error("kry_tridiag_expv_noalloc: bad arguments");
+        return KRY_EINVAL;
+    }
+    double *d = nullptr;
+    if (int rc = expv_scratch(&d)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *da = d, *db = d + MMAX, *dy = d + 2 * MMAX, *de = d + 4 * MMAX;
+    // Every element the kernel reads is copied in below and every element read back is
+    // written by the kernel, so nothing left over from an earlier call is used.
+    cudaError_t e = cudaMemcpyAsync(da, alpha, sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m > 1)
+        e = cudaMemcpyAsync(db, beta, sizeof(double) * (m - 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_expv_test, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(ExpSmem));
+    if (e == cudaSuccess) {
+        k_expv_test<<<1, 32, sizeof(ExpSmem), s>>>(da, db, m, h, tau, dy, de);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y_out, dy, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(err_out, de, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kry_tridiag_expv_noalloc");
+    return KRY_OK;
+}
