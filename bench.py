@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--form", default="c128", choices=["c128", "c64"],
+                    help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs): for ncu captures")
     a = ap.parse_args()
@@ -176,6 +178,46 @@ def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
     return per * D * krylov_steps
 
 
+def roofline(prof, form, D, c, L, N, clocks):
+    """Roofline of the dominant kernel kind over a profiled timed region.
+
+    complex128: every element costs FP64 arithmetic, and GB300's FP64 pipe (4 flop/clk/SM)
+    saturates before HBM, so the bound is the ALU; the HBM view is given beside it.
+    complex64: the bound is HBM."""
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
+    dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
+    per = {k: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / (v["ms"] * 1e6)) if v["ms"] else None,
+               "launches": v["launches"]} for k, v in prof.items()}
+    ach = prof[dom]["bytes"] / (prof[dom]["ms"] * 1e6)
+    nl = max(prof[dom]["launches"], 1)
+    hbm = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "peak_source": "measured" if peaks else "fallback"}
+    tr = ncu_traffic(dom, prof[dom]["bytes"] / nl) if form == "c128" else ncu_traffic_c64(dom, prof[dom]["bytes"] / nl)
+    share = {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values()) for k in KIND_NAMES}
+    if form == "c128":
+        # Krylov steps that did work (replays after the last output time are no-ops):
+        # recovered from the kind's algorithmic bytes, (j+2) or (j+3) vectors at index j
+        per_step = sum((j + 2) if dom == "passA" else (j + 3) for j in range(c["m"])) * D * 16
+        steps = prof[dom]["bytes"] / per_step
+        fl = fp64_flops(dom, D, c["m"], steps, L, N, c["pbc"])
+        mhz = clocks["sm_mhz"] or 2070.0
+        fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
+        ach_fl = fl / (prof[dom]["ms"] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
+                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
+                "traffic": tr, "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
+                "hbm_view": hbm, "per_kind": per, "kernel_time_share": share}
+    return dict(bound="hbm", kernel=dom, traffic=tr, algo_bytes_per_launch=prof[dom]["bytes"] / nl,
+                per_kind=per, kernel_time_share=share, **hbm)
+
+
+def ncu_traffic_c64(kind, algo_bytes_per_launch):
+    """As ncu_traffic, for the complex64 kernels (keys prefixed c64_)."""
+    return ncu_traffic("c64_" + kind, algo_bytes_per_launch)
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -223,15 +265,18 @@ def run_ours(args):
         H.profile(False)
         return e0.elapsed_time(e1) / 1e3, hv, launches, P, st, prof
 
+    form = args.form if args.kernels_only else "c128"
     clk = ClockSampler(local).start()
-    sec, hv, launches, P128, st128, prof = timed("c128", c["tol"], profile=True)
+    sec, hv, launches, P128, st128, prof = timed(form, c["tol"] if form == "c128" else 1e-7,
+                                                 profile=True)
     clocks = clk.stop()
     units, sec_all = aggregate(D * hv, sec, world)
     value = units / sec_all
     out = {"metric": METRIC, "value": value, "unit": "state-updates/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sec_all / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "c128 (fp64)" if form == "c128" else "c64 vectors, fp64 coefficients",
            "data": "synthetic (seeded quasiperiodic field, Neel state)"}
     cfg = {"workload": f"{args.workload}: L={L} N_up={N} D={D} PBC J=1 Delta=1 h=1.5 "
                        f"m={c['m']} tol={c['tol']:g} 40 log times in [0.1,100]",
@@ -240,41 +285,18 @@ def run_ours(args):
            "parallelism": f"replicas x{world}",
            "l2": "no flush: each step sweeps a 1.4 GB Krylov basis (31 vectors x 43 MB) > 129 MB L2"}
     # roofline of the dominant kernel kind, from CUDA events inside the timed region
-    peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
-    dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
-    per = {k: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / (v["ms"] * 1e6)) if v["ms"] else None,
-               "launches": v["launches"]} for k, v in prof.items()}
-    ach = prof[dom]["bytes"] / (prof[dom]["ms"] * 1e6)
-    nl = max(prof[dom]["launches"], 1)
-    tr = ncu_traffic(dom, prof[dom]["bytes"] / nl)
-    # The complex128 kernels issue FP64 arithmetic on every vector element; on GB300 the
-    # FP64 pipe (4 flop/clk/SM) saturates before HBM does, so their bound is the ALU.
-    fl = fp64_flops(dom, D, c["m"], hv // c["m"], L, N, c["pbc"])
-    mhz = clocks["sm_mhz"] or 2070.0
-    fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
-    ach_fl = fl / (prof[dom]["ms"] * 1e-3) / 1e12
-    out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
-                       "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
-                       "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
-                       "traffic": tr,
-                       "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
-                       "hbm_view": {"achieved": ach, "peak": peak, "unit": "GB/s",
-                                    "frac": ach / peak,
-                                    "peak_source": "measured" if peaks else "fallback"},
-                       "per_kind": per,
-                       "kernel_time_share": {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values())
-                                             for k in KIND_NAMES}}
+    out["roofline"] = roofline(prof, form, D, c, L, N, clocks)
     out["gpu_launches"] = launches
     out["clocks"] = clocks
     # mixed precision at the same stated accuracy target
     if not args.no_mixed:
-        sec64, hv64, l64, P64, st64, _ = timed("c64", 1e-7, profile=False)
+        sec64, hv64, l64, P64, st64, prof64 = timed("c64", 1e-7, profile=True)
         u64, s64 = aggregate(D * hv64, sec64, world)
         out["mixed"] = {"dtype": "c64 vectors, fp64 coefficients", "value": u64 / s64,
                         "unit": "state-updates/s", "ms_per_step": 1e3 * s64 / args.steps,
                         "speedup_vs_fp64": (u64 / s64) / value,
-                        "max_abs_dP_vs_fp64": float(np.max(np.abs(P64 - P128)))}
+                        "max_abs_dP_vs_fp64": float(np.max(np.abs(P64 - P128))),
+                        "tol": 1e-7, "roofline": roofline(prof64, "c64", D, c, L, N, clocks)}
         out["gpu_launches"] += l64
     out["config"] = cfg
     if args.kernels_only:
