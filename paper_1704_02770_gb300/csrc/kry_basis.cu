@@ -253,47 +253,52 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
     const int L = b->L;
     for (int i = 0; i < K * L; ++i)
         if (!std::isfinite(h[i])) { set_error("kry_hamiltonian_set: non-finite field"); return KRY_EINVAL; }
-    if (K != 1) {
-        set_error("kry_hamiltonian_set: K > 1 realisations are not supported by this build");
+    if (K > KBMAX) {
+        set_error("kry_hamiltonian_set: K = %d realisations exceeds the maximum %d", K, KBMAX);
         return KRY_EINVAL;
     }
     const int Llo = b->Llo, Lhi = b->Lhi;
     const uint32_t nlo = 1u << Llo, nhi = 1u << Lhi;
-    // field energy tables: sum_i h_i (n_i - 1/2) = ehlo[pos(lo)] + ehhi[hi]
+    // field energy tables, realisation fastest:
+    //   sum_i h_{k,i} (n_i - 1/2) = ehlo[pos(lo) * K + k] + ehhi[hi * K + k]
     std::vector<uint16_t> lolist(nlo);
     {
         std::vector<uint32_t> koff(Llo + 2, 0);
         for (int k = 0; k <= Llo; ++k) koff[k + 1] = koff[k] + (uint32_t)binom64(Llo, k);
         for (uint32_t lo = 0; lo < nlo; ++lo) lolist[koff[__builtin_popcount(lo)]++] = (uint16_t)lo;
     }
-    double hsum = 0.0;
-    for (int i = 0; i < L; ++i) hsum += h[i];
-    std::vector<double> ehlo(nlo), ehhi(nhi);
-    for (uint32_t p = 0; p < nlo; ++p) {
-        uint32_t lo = lolist[p];
-        double e = 0.0;
-        for (int i = 0; i < Llo; ++i) if ((lo >> i) & 1u) e += h[i];
-        ehlo[p] = e;
+    std::vector<double> ehlo((size_t)nlo * K), ehhi((size_t)nhi * K);
+    for (int k = 0; k < K; ++k) {
+        const double *hk = h + (size_t)k * L;
+        double hsum = 0.0;
+        for (int i = 0; i < L; ++i) hsum += hk[i];
+        for (uint32_t p = 0; p < nlo; ++p) {
+            uint32_t lo = lolist[p];
+            double e = 0.0;
+            for (int i = 0; i < Llo; ++i) if ((lo >> i) & 1u) e += hk[i];
+            ehlo[(size_t)p * K + k] = e;
+        }
+        for (uint32_t hi = 0; hi < nhi; ++hi) {
+            double e = -0.5 * hsum;
+            for (int q = 0; q < Lhi; ++q) if ((hi >> q) & 1u) e += hk[Llo + q];
+            ehhi[(size_t)hi * K + k] = e;
+        }
     }
-    for (uint32_t hi = 0; hi < nhi; ++hi) {
-        double e = -0.5 * hsum;
-        for (int q = 0; q < Lhi; ++q) if ((hi >> q) & 1u) e += h[Llo + q];
-        ehhi[hi] = e;
-    }
-    std::vector<float> ehlo_f(nlo), ehhi_f(nhi);
-    for (uint32_t p = 0; p < nlo; ++p) ehlo_f[p] = (float)ehlo[p];
-    for (uint32_t p = 0; p < nhi; ++p) ehhi_f[p] = (float)ehhi[p];
-    size_t o_ld = 0, o_hd = o_ld + 8 * (size_t)nlo, o_lf = o_hd + 8 * (size_t)nhi;
-    size_t o_hf = o_lf + 4 * (size_t)nlo, bytes = o_hf + 4 * (size_t)nhi;
+    std::vector<float> ehlo_f(ehlo.size()), ehhi_f(ehhi.size());
+    for (size_t p = 0; p < ehlo.size(); ++p) ehlo_f[p] = (float)ehlo[p];
+    for (size_t p = 0; p < ehhi.size(); ++p) ehhi_f[p] = (float)ehhi[p];
+    const size_t nl = (size_t)nlo * K, nh = (size_t)nhi * K;
+    size_t o_ld = 0, o_hd = o_ld + 8 * nl, o_lf = o_hd + 8 * nh;
+    size_t o_hf = o_lf + 4 * nl, bytes = o_hf + 4 * nh;
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
     cudaError_t e = cudaMalloc(&H->d_eh, bytes);
     if (e != cudaSuccess) { delete H; return cuda_fail(e, "cudaMalloc(field tables)"); }
     char *base = (char *)H->d_eh;
-    cudaMemcpy(base + o_ld, ehlo.data(), 8 * (size_t)nlo, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_hd, ehhi.data(), 8 * (size_t)nhi, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_lf, ehlo_f.data(), 4 * (size_t)nlo, cudaMemcpyHostToDevice);
-    e = cudaMemcpy(base + o_hf, ehhi_f.data(), 4 * (size_t)nhi, cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_ld, ehlo.data(), 8 * nl, cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_hd, ehhi.data(), 8 * nh, cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_lf, ehlo_f.data(), 4 * nl, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(base + o_hf, ehhi_f.data(), 4 * nh, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(H->d_eh); delete H; return cuda_fail(e, "field upload"); }
     H->b = b; H->J = J; H->Delta = Delta; H->K = K; H->boundary = boundary;
     H->h.assign(h, h + (size_t)K * L);
@@ -306,6 +311,7 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
     d.halfJ = 0.5 * J;
     d.pbc = (boundary == KRY_PBC && L >= 3) ? 1 : 0;
     d.nbonds = d.pbc ? L : (L - 1);
+    d.K = K;
     *out = H;
     return KRY_OK;
 }

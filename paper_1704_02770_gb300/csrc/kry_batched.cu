@@ -1,0 +1,591 @@
+// Batched realisations: K copies of Eq. 1 that differ only in the on-site field (K disorder
+// phases, Sec. 3 "many layers of disorder"), evolved together.  Vectors are interleaved
+// [state][K] complex, so one rank computation and one neighbour lookup serve K contiguous
+// amplitudes (a 512-byte row at K = 64 complex64).  Each realisation keeps its own Lanczos
+// recurrence (alpha_k, beta_k, reorthogonalisation coefficients) in FP64; all share the
+// time grid, so the step size is the smallest step every realisation accepts.
+//
+//   k_apply_b      y = H x for all K (warp per state, lanes over k)
+//   k_passA_b      u = H v_j with all dots <v_i, u> per realisation
+//   k_lincomb_b    update / correction / combine / load with per-realisation coefficients
+//   k_reduce_b     per-realisation sum of the per-CTA partials (CTA order, deterministic)
+//                  and the scalar epilogue of each pass
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kry_device.cuh"
+
+namespace kry {
+
+struct SmemHeadB {
+    uint32_t koff[20];
+    uint32_t bsz[20];
+};
+
+// Row r of H x for every realisation: the rank arithmetic is the same for all k, the
+// lanes of the warp run over k = lane + 32 q.
+template <class V, int KQ>
+__device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
+                                         int K, uint32_t hi, uint32_t off, int klo,
+                                         const uint32_t *koff_s, const uint16_t *rl, V out[KQ])
+{
+    using R = typename VT<V>::R;
+    const int lane = threadIdx.x & 31;
+    const int Llo = b.Llo, L = b.L;
+    const uint32_t pos = koff_s[klo] + off;
+    const uint32_t lo = __ldg(b.lolist + pos);
+    const uint32_t s = (hi << Llo) | lo;
+    const uint32_t base = __ldg(b.blk + hi);
+    const uint32_t lomask = (1u << Llo) - 1u;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint32_t anti = (s ^ (s >> 1)) & obc;
+    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
+    const int nanti = __popc(anti) + (int)wrap;
+    const R dz = (R)hm.cz * (R)(hm.nbonds - 2 * nanti);
+    V acc[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) acc[q] = VT<V>::zero();
+    auto gather = [&](uint32_t r2) {
+        const V *xr = x + (size_t)r2 * K;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            const int k = lane + 32 * q;
+            if (k < K) acc[q] = acc[q] + __ldg(xr + k);
+        }
+    };
+    uint32_t a = anti & ((1u << (Llo - 1)) - 1u);
+    while (a) {
+        const int p = __ffs(a) - 1;
+        a &= a - 1u;
+        gather(base + rl[lo ^ (3u << p)]);
+    }
+    if (b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u)) {
+        const uint32_t s2 = s ^ (3u << (Llo - 1));
+        gather(__ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    uint32_t ah = anti >> Llo;
+    while (ah) {
+        const int q = __ffs(ah) - 1;
+        ah &= ah - 1u;
+        gather(__ldg(b.blk + (hi ^ (3u << q))) + off);
+    }
+    if (wrap) {
+        const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
+        gather(__ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    const V *xr = x + (size_t)(base + off) * K;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int k = lane + 32 * q;
+        if (k < K) {
+            const R d = dz + VT<V>::ehlo(hm, pos * K + k) + VT<V>::ehhi(hm, hi * K + k);
+            out[q] = axpby(d, __ldg(xr + k), (R)hm.halfJ, acc[q]);
+        } else {
+            out[q] = VT<V>::zero();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- y = H x (batched)
+
+template <class V, int KQ>
+__global__ void __launch_bounds__(NTHR) k_apply_b(DevBasis b, DevHam hm, int K, const V *__restrict__ x,
+                                                  V *__restrict__ y, int rl_smem)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemHeadB *hd = (SmemHeadB *)smem;
+    uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHeadB));
+    stage_tables(b, hd->koff, hd->bsz, rl_s, rl_smem);
+    __syncthreads();
+    const uint16_t *rl = rl_smem ? rl_s : b.ranklo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TROWS;
+        for (int rr = warp; rr < TROWS; rr += NTHR / 32) {
+            if (r0 + rr >= b.D) break;
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(b, hd->bsz, r0, rr, hi, off, klo);
+            V u[KQ];
+            hv_row_b<V, KQ>(b, hm, x, K, hi, off, klo, hd->koff, rl, u);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int k = lane + 32 * q;
+                if (k < K) y[(size_t)(r0 + rr) * K + k] = u[q];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- pass A (batched)
+
+template <class V, int KQ>
+__global__ void __launch_bounds__(NTHR, 1) k_passA_b(EvArgsB<V> a, int jj)
+{
+    KryCtlB *ctl = a.ctl;
+    if (ctl->hd.done || jj >= ctl->hd.m_run) return;
+    constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *utile = (V *)smem;                                        // [TROWS][Kp]
+    double *nred = (double *)(utile + TROWS * Kp);               // [8][Kp]
+    double *sig = nred + (NTHR / 32) * Kp;                       // [Kp]
+    SmemHeadB *hd = (SmemHeadB *)(sig + Kp);
+    uint16_t *rl_s = (uint16_t *)(hd + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K;
+    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
+    for (int k = tid; k < Kp; k += NTHR) sig[k] = (k < K) ? ctl->sigma[jj][k] : 0.0;
+    __syncthreads();
+    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
+    const V *x = a.W + (size_t)jj * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
+    const int kd = tid % Kp, gd = tid / Kp;   // dot phase: column kd, vectors i = gd + NG q
+    DotAcc<V> acc[QD];
+    DotAcc<V> nrm[KQ];
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TROWS;
+        for (int rr = warp; rr < TROWS; rr += NTHR / 32) {
+            V u[KQ];
+            if (r0 + rr < D) {
+                uint32_t hi, off;
+                int klo;
+                tile_unrank(a.b, hd->bsz, r0, rr, hi, off, klo);
+                hv_row_b<V, KQ>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u);
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    const int k = lane + 32 * q;
+                    u[q] = scale(u[q], sig[k]);
+                    if (k < K) a.U[(size_t)(r0 + rr) * K + k] = u[q];
+                    nrm[q].add(u[q], u[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) u[q] = VT<V>::zero();
+            }
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) utile[rr * Kp + lane + 32 * q] = u[q];
+        }
+        __syncthreads();
+        if (kd < K) {
+#pragma unroll
+            for (int q = 0; q < QD; ++q) {
+                const int iv = gd + NG * q;
+                if (iv <= jj) {
+                    const V *wi = a.W + (size_t)iv * a.ldW + (size_t)r0 * K + kd;
+                    V vv[TROWS];
+#pragma unroll
+                    for (int rr = 0; rr < TROWS; ++rr)
+                        vv[rr] = (r0 + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+#pragma unroll
+                    for (int rr = 0; rr < TROWS; ++rr) acc[q].add(vv[rr], utile[rr * Kp + kd]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    double2 *pc = a.part + (size_t)blockIdx.x * PSB * Kp;
+#pragma unroll
+    for (int q = 0; q < QD; ++q) {
+        const int iv = gd + NG * q;
+        if (iv <= jj) pc[(size_t)iv * Kp + kd] = acc[q].value();
+    }
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) nred[warp * Kp + lane + 32 * q] = nrm[q].value().x;
+    __syncthreads();
+    for (int k = tid; k < Kp; k += NTHR) {
+        double s = 0.0;
+        for (int w = 0; w < NTHR / 32; ++w) s += nred[w * Kp + k];
+        pc[(size_t)SLOT_NRM * Kp + k] = make_double2(s, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------- linear combinations (batched)
+
+template <class V, int MODE, int KQ>
+__global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
+{
+    KryCtlB *ctl = a.ctl;
+    if (ctl->hd.done) return;
+    if (MODE <= 1 && jj >= ctl->hd.m_run) return;
+    if (MODE == 1 && !ctl->hd.corr_any) return;
+    constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
+    const int nvec = (MODE == 2) ? ctl->hd.m_run : ((MODE == 3) ? 0 : jj + 1);
+    extern __shared__ __align__(16) unsigned char smem[];
+    V *coef = (V *)smem;                          // [MMAX+1][Kp]
+    V *wtile = coef + (MMAX + 1) * Kp;            // [TROWS][Kp]
+    double2 *nred = (double2 *)(wtile + TROWS * Kp);   // [NG][Kp] (norm), then [NG][Kp] (G)
+    const int tid = threadIdx.x, K = a.K;
+    for (int e = tid; e < nvec * Kp; e += NTHR) {
+        const int i = e / Kp, k = e % Kp;
+        double2 c = make_double2(0.0, 0.0);
+        if (k < K) c = (MODE == 0) ? ctl->coefA[i][k] : (MODE == 1) ? ctl->coefC[i][k] : ctl->coefY[i][k];
+        coef[i * Kp + k] = VT<V>::from(c);
+    }
+    __syncthreads();
+    V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
+    const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
+    const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
+    const int k = tid % Kp, g = tid / Kp;
+    DotAcc<V> acc[QD];
+    DotAcc<V> nrm, gacc;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TROWS;
+        for (int rr = g; rr < TROWS; rr += NG) {
+            V w = VT<V>::zero();
+            if (r0 + rr < D && k < K) {
+                const size_t idx = (size_t)(r0 + rr) * K + k;
+                if (src) w = src[idx];
+                if (MODE == 2) {
+#pragma unroll 8
+                    for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], a.W[(size_t)i * a.ldW + idx], w);
+                } else {
+#pragma unroll 8
+                    for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], __ldg(a.W + (size_t)i * a.ldW + idx), w);
+                }
+                out[idx] = w;
+                nrm.add(w, w);
+                if (a.G && MODE != 3) gacc.add(__ldg(a.G + idx), w);
+            }
+            if (MODE == 0) wtile[rr * Kp + k] = w;
+        }
+        if (MODE == 0) {
+            __syncthreads();
+            if (k < K) {
+#pragma unroll
+                for (int q = 0; q < QD; ++q) {
+                    const int iv = g + NG * q;
+                    if (iv <= jj) {
+                        const V *wi = a.W + (size_t)iv * a.ldW + (size_t)r0 * K + k;
+                        V vv[TROWS];
+#pragma unroll
+                        for (int rr = 0; rr < TROWS; ++rr)
+                            vv[rr] = (r0 + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+#pragma unroll
+                        for (int rr = 0; rr < TROWS; ++rr) acc[q].add(vv[rr], wtile[rr * Kp + k]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    double2 *pc = a.part + (size_t)blockIdx.x * PSB * Kp;
+    if (MODE == 0) {
+#pragma unroll
+        for (int q = 0; q < QD; ++q) {
+            const int iv = g + NG * q;
+            if (iv <= jj) pc[(size_t)iv * Kp + k] = acc[q].value();
+        }
+    }
+    nred[g * Kp + k] = nrm.value();
+    nred[(NG + g) * Kp + k] = gacc.value();
+    __syncthreads();
+    for (int kk = tid; kk < Kp; kk += NTHR) {
+        double2 s = make_double2(0.0, 0.0), t = make_double2(0.0, 0.0);
+        for (int gg = 0; gg < NG; ++gg) {
+            s.x += nred[gg * Kp + kk].x;
+            t.x += nred[(NG + gg) * Kp + kk].x;
+            t.y += nred[(NG + gg) * Kp + kk].y;
+        }
+        pc[(size_t)SLOT_NRM * Kp + kk] = s;
+        pc[(size_t)SLOT_G * Kp + kk] = t;
+    }
+}
+
+// ---------------------------------------------------------------- per-realisation reductions
+
+// mode: 0 pass A, 1 pass B, 2 pass C, 4 combine, 5 load of a general psi0.
+__global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *__restrict__ part,
+                                                  int grid, int Kp, int mode, int jj, int general)
+{
+    KryHdrB &H = ctl->hd;
+    if (H.done) return;
+    if ((mode == 0 || mode == 1 || mode == 2) && jj >= H.m_run) return;
+    const int k = blockIdx.x, tid = threadIdx.x;
+    const bool corr_pass = (mode == 2);
+    if (corr_pass && !H.corr_any) return;   // pass C did not run
+    __shared__ double2 red[128];
+    __shared__ double2 fin[PSB];
+    const int nd = (mode == 0 || mode == 1) ? jj + 1 : 0;
+    auto reduce_slot = [&](int slot) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int c = tid; c < grid; c += 128) {
+            const double2 v = __ldg(part + ((size_t)c * PSB + slot) * Kp + k);
+            s.x += v.x;
+            s.y += v.y;
+        }
+        red[tid] = s;
+        __syncthreads();
+        for (int o = 64; o > 0; o >>= 1) {
+            if (tid < o) { red[tid].x += red[tid + o].x; red[tid].y += red[tid + o].y; }
+            __syncthreads();
+        }
+        if (tid == 0) fin[slot] = red[0];
+        __syncthreads();
+    };
+    for (int i = 0; i < nd; ++i) reduce_slot(i);
+    reduce_slot(SLOT_NRM);
+    if (general && mode != 0) reduce_slot(SLOT_G);
+    if (tid != 0) return;
+    const double nw2 = fin[SLOT_NRM].x;
+    const double2 gdot = (general && mode != 0) ? fin[SLOT_G] : make_double2(0.0, 0.0);
+    auto finalize = [&](double w2, double2 gd) {
+        const double bt = sqrt(w2);
+        ctl->beta[jj][k] = bt;
+        if (!(bt > H.eta_bd * sqrt(ctl->normu2[k]))) {
+            ctl->m_eff[k] = jj + 1;
+            atomicAdd(&H.n_bd, 1ull);
+            ctl->sigma[jj + 1][k] = 0.0;
+        } else {
+            const double s = 1.0 / bt;
+            ctl->sigma[jj + 1][k] = s;
+            ctl->g[jj + 1][k] = make_double2(gd.x * s, gd.y * s);
+        }
+    };
+    if (mode == 0) {
+        if (k == 0) {
+            H.n_hv += 1;
+            H.vec_passes += (double)(jj + 2);
+            H.vp_kind[0] += (double)(jj + 2);
+            H.corr_any = 0;
+        }
+        if (jj >= ctl->m_eff[k]) {
+            // invariant subspace already reached: this realisation's next vectors stay zero
+            for (int i = 0; i <= jj; ++i) ctl->coefA[i][k] = make_double2(0.0, 0.0);
+            return;
+        }
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i][k];
+            const double2 c = make_double2(fin[i].x * s, fin[i].y * s);
+            ctl->coefA[i][k] = make_double2(c.x * s, c.y * s);
+            if (i == jj) ctl->alpha[jj][k] = c.x;
+        }
+        ctl->normu2[k] = nw2;
+    } else if (mode == 1) {
+        if (k == 0) {
+            H.vec_passes += (double)(jj + 3) + (general ? 1.0 : 0.0);
+            H.vp_kind[1] += (double)(jj + 3) + (general ? 1.0 : 0.0);
+        }
+        ctl->corr[k] = 0;
+        if (jj >= ctl->m_eff[k]) return;
+        double nd2 = 0.0;
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i][k];
+            nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
+        }
+        if (nw2 > 0.0) ctl->orth[k] = fmax(ctl->orth[k], sqrt(nd2 / nw2));
+        if (nw2 > 0.0 && sqrt(nd2) > H.eta_corr * sqrt(nw2)) {
+            ctl->corr[k] = 1;
+            H.corr_any = 1;
+            for (int i = 0; i <= jj; ++i) {
+                const double s = ctl->sigma[i][k];
+                ctl->coefC[i][k] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
+            }
+            for (int i = jj + 1; i <= MMAX; ++i) ctl->coefC[i][k] = make_double2(0.0, 0.0);
+            ctl->alpha[jj][k] += fin[jj].x * ctl->sigma[jj][k];
+        } else {
+            for (int i = 0; i <= jj; ++i) ctl->coefC[i][k] = make_double2(0.0, 0.0);
+            finalize(nw2, gdot);
+        }
+    } else if (mode == 2) {
+        if (k == 0) {
+            H.vec_passes += (double)(jj + 3) + (general ? 1.0 : 0.0);
+            H.vp_kind[2] += (double)(jj + 3) + (general ? 1.0 : 0.0);
+        }
+        if (jj < ctl->m_eff[k] && ctl->corr[k]) {
+            atomicAdd(&H.n_corr, 1ull);
+            finalize(nw2, gdot);
+        }
+    } else {   // 4 combine, 5 load of psi0
+        const double b0 = sqrt(nw2);
+        if (!(b0 > 0.0)) {
+            H.err = KRY_EINVAL;
+            H.done = 1;
+            return;
+        }
+        ctl->beta0[k] = b0;
+        ctl->sigma[0][k] = 1.0 / b0;
+        ctl->g[0][k] = (mode == 5) ? make_double2(b0, 0.0) : make_double2(gdot.x / b0, gdot.y / b0);
+        ctl->m_eff[k] = H.m;
+        ctl->corr[k] = 0;
+    }
+}
+
+// Shared bookkeeping after the combine (one thread): advance time, count the step.
+__global__ void k_step_done_b(KryCtlB *ctl, int general)
+{
+    KryHdrB &H = ctl->hd;
+    if (H.done) return;
+    double e = 0.0;
+    for (int k = 0; k < H.K; ++k) e = fmax(e, ctl->err_k[k]);
+    H.err_sum += e;
+    H.n_steps += 1;
+    H.vec_passes += (double)(H.m_run + 1) + (general ? 1.0 : 0.0);
+    H.vp_kind[4] += (double)(H.m_run + 1) + (general ? 1.0 : 0.0);
+    H.t_now = H.t_next;
+    H.next_out = H.next_out_new;
+    H.m_run = H.m;
+    H.corr_any = 0;
+    if (H.finishing) H.done = 1;
+}
+
+// m_run refresh after pass C ran (all per-realisation epilogues of pass C are complete).
+__global__ void k_mrun_b(KryCtlB *ctl)
+{
+    KryHdrB &H = ctl->hd;
+    if (H.done) return;
+    int mr = 0;
+    for (int k = 0; k < H.K; ++k) mr = max(mr, ctl->m_eff[k]);
+    H.m_run = mr;
+}
+
+template <class V>
+__global__ void k_set_basis_state_b(V *W0, int K, uint32_t r0)
+{
+    const int k = threadIdx.x;
+    if (k < K) {
+        V one = VT<V>::zero();
+        one.x = 1;
+        W0[(size_t)r0 * K + k] = one;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int sm_count_b()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static size_t passA_b_smem(const DevBasis &b, int Kp, int rl_smem, size_t es)
+{
+    return es * TROWS * Kp + sizeof(double) * (NTHR / 32) * Kp + sizeof(double) * Kp + sizeof(SmemHeadB) +
+           (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
+}
+
+static size_t lincomb_b_smem(int Kp, size_t es)
+{
+    return es * (MMAX + 1) * Kp + es * TROWS * Kp + sizeof(double2) * 2 * NTHR;
+}
+
+template <class K_>
+static int set_smem(K_ kernel, size_t smem)
+{
+    if (smem > 48 * 1024) KRY_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return KRY_OK;
+}
+
+#define KRY_KQ_SWITCH(Kp, ...)                                \
+    switch (Kp) {                                             \
+    case 32: { constexpr int KQ = 1; __VA_ARGS__; } break;    \
+    case 64: { constexpr int KQ = 2; __VA_ARGS__; } break;    \
+    default: { constexpr int KQ = 4; __VA_ARGS__; } break;    \
+    }
+
+template <class V>
+int batched_grid(const DevBasis &b, int Kp, int rl_smem)
+{
+    const size_t es = sizeof(V);
+    int occ = 1;
+    KRY_KQ_SWITCH(Kp, {
+        const size_t sA = passA_b_smem(b, Kp, rl_smem, es);
+        if (int rc = set_smem(k_passA_b<V, KQ>, sA)) return -rc;
+        int o1 = 0, o2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_passA_b<V, KQ>, NTHR, sA);
+        const size_t sL = lincomb_b_smem(Kp, es);
+        if (int rc = set_smem(k_lincomb_b<V, 0, KQ>, sL)) return -rc;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lincomb_b<V, 0, KQ>, NTHR, sL);
+        occ = std::max(1, std::min(o1, o2));
+    });
+    const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
+    return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * occ)));
+}
+
+template <class V>
+int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
+{
+    const size_t sA = passA_b_smem(a.b, a.Kp, a.rl_smem, sizeof(V));
+    KRY_KQ_SWITCH(a.Kp, { k_passA_b<V, KQ><<<grid, NTHR, sA, s>>>(a, jj); });
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template <class V>
+int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream_t s)
+{
+    const size_t sL = lincomb_b_smem(a.Kp, sizeof(V));
+    KRY_KQ_SWITCH(a.Kp, {
+        switch (mode) {
+        case 0: if (int rc = set_smem(k_lincomb_b<V, 0, KQ>, sL)) return rc; k_lincomb_b<V, 0, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
+        case 1: if (int rc = set_smem(k_lincomb_b<V, 1, KQ>, sL)) return rc; k_lincomb_b<V, 1, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
+        case 2: if (int rc = set_smem(k_lincomb_b<V, 2, KQ>, sL)) return rc; k_lincomb_b<V, 2, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
+        default: if (int rc = set_smem(k_lincomb_b<V, 3, KQ>, sL)) return rc; k_lincomb_b<V, 3, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
+        }
+    });
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+// mode 0..2 follow passes A..C; 4 the combine (then the shared step bookkeeping);
+// 5 the load of a general psi0.
+int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, int mode, int jj,
+                    int general, double, cudaStream_t s)
+{
+    k_reduce_b<<<K, 128, 0, s>>>(ctl, part, grid, Kp, mode, jj, general);
+    KRY_CU(cudaGetLastError());
+    if (mode == 2) {
+        k_mrun_b<<<1, 1, 0, s>>>(ctl);
+        KRY_CU(cudaGetLastError());
+    }
+    if (mode == 4) {
+        k_step_done_b<<<1, 1, 0, s>>>(ctl, general);
+        KRY_CU(cudaGetLastError());
+    }
+    return KRY_OK;
+}
+
+int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
+                   int rl_smem, cudaStream_t s)
+{
+    int Kp = 32;
+    while (Kp < K) Kp *= 2;
+    const size_t smem = sizeof(SmemHeadB) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
+    const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
+    const int grid = (int)std::min<uint32_t>(ntiles, (uint32_t)sm_count_b() * 8u);
+    KRY_KQ_SWITCH(Kp, {
+        if (c64) {
+            if (int rc = set_smem(k_apply_b<float2, KQ>, smem)) return rc;
+            k_apply_b<float2, KQ><<<grid, NTHR, smem, s>>>(b, h, K, (const float2 *)x, (float2 *)y, rl_smem);
+        } else {
+            if (int rc = set_smem(k_apply_b<double2, KQ>, smem)) return rc;
+            k_apply_b<double2, KQ><<<grid, NTHR, smem, s>>>(b, h, K, (const double2 *)x, (double2 *)y, rl_smem);
+        }
+    });
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t s)
+{
+    if (c64) k_set_basis_state_b<float2><<<1, KBMAX, 0, s>>>((float2 *)W0, K, r0);
+    else k_set_basis_state_b<double2><<<1, KBMAX, 0, s>>>((double2 *)W0, K, r0);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template int batched_grid<double2>(const DevBasis &, int, int);
+template int batched_grid<float2>(const DevBasis &, int, int);
+template int launch_passA_b<double2>(const EvArgsB<double2> &, int, int, cudaStream_t);
+template int launch_passA_b<float2>(const EvArgsB<float2> &, int, int, cudaStream_t);
+template int launch_lincomb_b<double2>(const EvArgsB<double2> &, int, int, int, cudaStream_t);
+template int launch_lincomb_b<float2>(const EvArgsB<float2> &, int, int, int, cudaStream_t);
+
+}  // namespace kry

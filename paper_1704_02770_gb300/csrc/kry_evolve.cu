@@ -266,6 +266,250 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     return KRY_OK;
 }
 
+// ---------------------------------------------------------------- batched realisations
+
+int padded_k(int K)
+{
+    int Kp = 32;
+    while (Kp < K) Kp *= 2;
+    return Kp;
+}
+
+Layout layout_b(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
+{
+    Layout l{};
+    const size_t es = elem_size(dtype);
+    const size_t n = (size_t)H->b->D * (size_t)H->K;
+    const int Kp = padded_k(H->K);
+    l.ldW = round_up(n, 64);
+    l.oW = 0;
+    l.oU = l.oW + (size_t)(m + 1) * l.ldW * es;
+    l.oG = l.oU + l.ldW * es;
+    l.oPart = l.oG + l.ldW * es;
+    l.oCtl = round_up(l.oPart + (size_t)grid * PSB * Kp * sizeof(double2), 256);
+    l.oTimes = round_up(l.oCtl + sizeof(KryCtlB), 256);
+    l.oP = round_up(l.oTimes + sizeof(double) * (size_t)n_times, 256);
+    l.bytes = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    return l;
+}
+
+int grid_for_b(const kry_ham_s *H, int dtype)
+{
+    const DevBasis &b = H->b->dev;
+    const int Kp = padded_k(H->K);
+    return dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b)) : batched_grid<double2>(b, Kp, rl_in_smem(b));
+}
+
+// One Krylov step of the batched path, in groups whose boundaries carry the profile events:
+// per Lanczos index {pass A, reduce}, {pass B, reduce}, {pass C, reduce, m_run};
+// then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
+template <class V>
+int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m, int grid, int general)
+{
+    cudaStream_t cs = H->cap_stream;
+    cudaGraph_t g = nullptr;
+    const int nk = 3 * m + 2;
+    if (H->prof_on) {
+        H->prof_ev.resize(nk + 1);
+        for (auto &e : H->prof_ev) KRY_CU(cudaEventCreate(&e));
+    }
+    KRY_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = KRY_OK, k = 0;
+    auto mark = [&]() {
+        if (H->prof_on && rc == KRY_OK) {
+            cudaError_t er = cudaEventRecordWithFlags(H->prof_ev[k], cs, cudaEventRecordExternal);
+            if (er != cudaSuccess) rc = cuda_fail(er, "cudaEventRecord(capture)");
+        }
+        ++k;
+    };
+    const double2 *part = a.part;
+    for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
+        mark();
+        rc = launch_passA_b<V>(a, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 0, jj, general, 0, cs);
+        mark();
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 0, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 1, jj, general, 0, cs);
+        mark();
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 1, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 2, jj, general, 0, cs);
+    }
+    mark();
+    if (rc == KRY_OK) rc = launch_exp_b(ea, cs);
+    mark();
+    if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 2, 0, grid, cs);
+    if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 4, 0, general, 0, cs);
+    mark();
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&H->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { H->gexec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return KRY_OK;
+}
+
+template <class V>
+int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool general,
+              const double *times, int n_times, int m, double tol, void *d_psi_out, double *P_out,
+              kry_stats *st, cudaStream_t s)
+{
+    const DevBasis &b = H->b->dev;
+    const int K = H->K, Kp = padded_k(K);
+    const int grid = grid_for_b(H, dtype);
+    if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
+    const Layout l = layout_b(H, dtype, m, grid, n_times);
+    if (!H->ws || H->ws_bytes < l.bytes) {
+        drop_graph(H);
+        if (H->ws) cudaFree(H->ws);
+        H->ws = nullptr;
+        H->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&H->ws, l.bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+        H->ws_bytes = l.bytes;
+    }
+    if (!H->cap_stream) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    if (!H->h_poll) KRY_CU(cudaMallocHost(&H->h_poll, sizeof(KryCtl) > sizeof(KryHdrB) ? sizeof(KryCtl) : sizeof(KryHdrB)));
+    char *base = (char *)H->ws;
+    EvArgsB<V> a{};
+    a.b = b;
+    a.h = H->dev;
+    a.W = (V *)(base + l.oW);
+    a.ldW = l.ldW;
+    a.U = (V *)(base + l.oU);
+    a.G = general ? (const V *)(base + l.oG) : nullptr;
+    a.part = (double2 *)(base + l.oPart);
+    a.ctl = (KryCtlB *)(base + l.oCtl);
+    a.K = K;
+    a.Kp = Kp;
+    a.rl_smem = rl_in_smem(b);
+    ExpArgsB ea{};
+    ea.ctl = a.ctl;
+    ea.times = (const double *)(base + l.oTimes);
+    ea.P = (double *)(base + l.oP);
+    ea.W = a.W;
+    ea.ldW = l.ldW;
+    ea.c64 = dtype == KRY_C64;
+    ea.K = K;
+    const int gkey = 2 + (int)general;   // distinguishes batched graphs from single ones
+    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != gkey ||
+                     H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
+                     (int)H->prof_ev.empty() == H->prof_on))
+        drop_graph(H);
+    if (!H->gexec) {
+        if (int rc = capture_step_b<V>(H, a, ea, m, grid, (int)general)) return rc;
+        H->g_dtype = dtype; H->g_m = m; H->g_general = gkey; H->g_grid = grid;
+        H->g_ws = H->ws; H->g_G = base + l.oP;
+    }
+    cudaEvent_t ev0, ev1;
+    KRY_CU(cudaEventCreate(&ev0));
+    KRY_CU(cudaEventCreate(&ev1));
+    KRY_CU(cudaEventRecord(ev0, s));
+    KryCtlB *c = new (std::nothrow) KryCtlB();
+    if (!c) { set_error("kry_evolve: host allocation failed"); return KRY_ENOMEM; }
+    std::memset(c, 0, sizeof(KryCtlB));
+    KryHdrB &hd = c->hd;
+    hd.K = K;
+    hd.m = m;
+    hd.m_run = m;
+    hd.t_end = times[n_times - 1];
+    hd.tol = tol;
+    hd.n_times = n_times;
+    hd.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
+    hd.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
+    for (int k = 0; k < K; ++k) c->m_eff[k] = m;
+    const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)K;
+    uint32_t r0 = 0;
+    if (general) {
+        hd.r0 = -1;
+    } else {
+        uint64_t r = 0;
+        int j = 0;
+        for (int p = 0; p < b.L; ++p)
+            if ((state >> p) & 1ull) r += binom_host(p, ++j);
+        r0 = (uint32_t)r;
+        hd.r0 = (int)r;
+        for (int k = 0; k < K; ++k) {
+            c->beta0[k] = 1.0;
+            c->sigma[0][k] = 1.0;
+            c->g[0][k] = make_double2(1.0, 0.0);
+        }
+    }
+    cudaError_t ce = cudaMemcpyAsync(a.ctl, c, sizeof(KryCtlB), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);   // c is freed next
+    delete c;
+    if (ce != cudaSuccess) return cuda_fail(ce, "control block upload");
+    KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
+    if (general) {
+        KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        if (int rc = launch_lincomb_b<V>(a, 3, 0, grid, s)) return rc;
+        if (int rc = launch_reduce_b(a.ctl, a.part, grid, K, Kp, 5, 0, 1, 0, s)) return rc;
+    } else {
+        KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
+        if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, r0, s)) return rc;
+    }
+    KryHdrB *hp = (KryHdrB *)H->h_poll;
+    long long launched = 0;
+    const long long max_launch = 500000;   // Krylov steps before KRY_ETIMEOUT
+    const int nk = 3 * m + 2;
+    int batch = 1;
+    for (;;) {
+        if (H->prof_on) batch = 1;
+        for (int i = 0; i < batch; ++i) KRY_CU(cudaGraphLaunch(H->gexec, s));
+        launched += batch;
+        KRY_CU(cudaMemcpyAsync(hp, &a.ctl->hd, sizeof(KryHdrB), cudaMemcpyDeviceToHost, s));
+        KRY_CU(cudaStreamSynchronize(s));
+        if (H->prof_on) {
+            for (int k = 0; k < nk; ++k) {
+                float ms = 0.f;
+                KRY_CU(cudaEventElapsedTime(&ms, H->prof_ev[k], H->prof_ev[k + 1]));
+                H->prof_ms[kind_of(k, m)] += ms;
+                H->prof_launches[kind_of(k, m)] += 1;
+            }
+        }
+        if (hp->done) break;
+        if (launched >= max_launch) {
+            set_error("kry_evolve: no convergence after %lld Krylov steps (t = %g of %g)", launched,
+                      hp->t_now, hp->t_end);
+            return KRY_ETIMEOUT;
+        }
+        const double rem = hp->t_end - hp->t_now;
+        const double est = (hp->t_next > 0.0 && hp->n_steps > 0) ? rem / (hp->t_now / (double)hp->n_steps) : 1.0;
+        batch = (int)std::min(64.0, std::max(1.0, std::ceil(est * 1.05)));
+    }
+    KRY_CU(cudaEventRecord(ev1, s));
+    if (H->prof_on)
+        for (int q = 0; q < NKIND; ++q) H->prof_bytes[q] += hp->vp_kind[q] * (double)nvec * (double)es;
+    if (hp->err) {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
+        else set_error("kry_evolve: an initial vector has zero norm");
+        return hp->err;
+    }
+    KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * K, cudaMemcpyDeviceToHost, s));
+    if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> orth(K);
+    KRY_CU(cudaMemcpyAsync(orth.data(), a.ctl->orth, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    KRY_CU(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (st) {
+        st->n_hv = (int64_t)hp->n_hv;
+        st->n_krylov_steps = (int64_t)hp->n_steps;
+        st->n_second_pass = (int64_t)hp->n_corr;
+        st->n_breakdowns = (int64_t)hp->n_bd;
+        st->err_estimate = hp->err_sum;
+        st->max_orth_loss = *std::max_element(orth.begin(), orth.end());
+        st->time_ms = ms;
+        st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
+        st->n_launches = launched * (7 * m + 5) + (general ? 2 : 1);
+    }
+    return KRY_OK;
+}
+
 int check_evolve_args(kry_ham H, int dtype, const double *times, int n_times, int m, double tol,
                       double *P_out)
 {
@@ -327,6 +571,8 @@ extern "C" int kry_apply(kry_ham H, int dtype, const void *d_x, void *d_y, void 
         return KRY_EINVAL;
     }
     const DevBasis &b = H->b->dev;
+    if (H->K > 1)
+        return launch_apply_b(b, H->dev, dtype == KRY_C64, H->K, d_x, d_y, rl_in_smem(b), (cudaStream_t)stream);
     return launch_apply(b, H->dev, dtype == KRY_C64, d_x, d_y, rl_in_smem(b), (cudaStream_t)stream);
 }
 
@@ -338,8 +584,12 @@ extern "C" int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double
     if (!d_psi0) { set_error("kry_evolve: d_psi0 is NULL"); return KRY_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C64)
-        return evolve_t<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
-    return evolve_t<double2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+        return H->K > 1
+                   ? evolve_bt<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
+                   : evolve_t<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+    return H->K > 1
+               ? evolve_bt<double2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
+               : evolve_t<double2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
 }
 
 extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const double *times,
@@ -354,6 +604,10 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C64)
-        return evolve_t<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
-    return evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+        return H->K > 1
+                   ? evolve_bt<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
+                   : evolve_t<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+    return H->K > 1
+               ? evolve_bt<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
+               : evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
 }

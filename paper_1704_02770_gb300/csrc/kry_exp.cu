@@ -336,6 +336,201 @@ __global__ void __launch_bounds__(32) k_expv_test(const double *alpha, const dou
     }
 }
 
+// ---------------------------------------------------------------- batched realisations
+// Every realisation k has its own T_k, coupling h_k and norm beta_k.  k_exp_scan_b finds,
+// per realisation, the largest ladder step that meets the error budget; k_exp_apply_b takes
+// the smallest of those (the leading error term grows with the step, so every realisation
+// stays within its budget), builds exp(-i tau T_k) e_1 for the combine and reads P_k at
+// every output time inside the step.
+
+__device__ void load_tridiag_b(ExpSmem &sm, const KryCtlB *ctl, int k, int me, const ExpArgsB &ea)
+{
+    const int lane = threadIdx.x;
+    if (lane < me) {
+        sm.al[lane] = ctl->alpha[lane][k];
+        sm.be[lane] = ctl->beta[lane][k];
+        double2 g;
+        if (ctl->hd.r0 >= 0) {
+            const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->hd.r0 * ea.K + k;
+            double2 w;
+            if (ea.c64) { float2 f = ((const float2 *)ea.W)[idx]; w = make_double2(f.x, f.y); }
+            else w = ((const double2 *)ea.W)[idx];
+            const double s = ctl->sigma[lane][k];
+            g = make_double2(w.x * s, w.y * s);
+        } else {
+            g = ctl->g[lane][k];
+        }
+        sm.g[lane] = g;
+    }
+    __syncwarp();
+}
+
+__device__ double2 gershgorin(const ExpSmem &sm, int me)
+{
+    const int j = threadIdx.x;
+    const double a = (j < me) ? sm.al[j] : 0.0;
+    const double bl = (j >= 1 && j < me) ? fabs(sm.be[j - 1]) : 0.0;
+    const double br = (j + 1 < me) ? fabs(sm.be[j]) : 0.0;
+    double lo = (j < me) ? a - bl - br : 1e300, hi = (j < me) ? a + bl + br : -1e300;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double r = 0.5 * (hi - lo);
+    const double rmin = 1e-12 * fmax(1.0, fmax(fabs(lo), fabs(hi)));
+    return make_double2(0.5 * (lo + hi), r > rmin ? r : rmin);
+}
+
+__global__ void __launch_bounds__(32) k_exp_scan_b(ExpArgsB ea)
+{
+    KryCtlB *ctl = ea.ctl;
+    const KryHdrB &H = ctl->hd;
+    if (H.done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ExpSmem &sm = *(ExpSmem *)smem_raw;
+    const int k = blockIdx.x, lane = threadIdx.x;
+    const int me = ctl->m_eff[k];
+    load_tridiag_b(sm, ctl, k, me, ea);
+    const double beta0 = ctl->beta0[k], h = sm.be[me - 1];
+    const double remaining = H.t_end - H.t_now;
+    double2 cr = gershgorin(sm, me);
+    const double tau_hi = fmin(remaining, XMAX / cr.y);
+    const int Kc = cheb_degree(tau_hi * cr.y);
+    cr = chebyshev_basis(sm, me, Kc);
+    const double r = cr.y;
+    double *myJ = sm.jb + lane * (KMAX + 2);
+    double tau_top = tau_hi, tau = 0.0;
+    int pick = -1;
+    for (int round = 0; round < 4 && pick < 0; ++round) {
+        const double tq = tau_top * pow(LADDER, (double)lane);
+        bessel_seq(tq * r, Kc, myJ);
+        double eq = 0.0;
+        if (h != 0.0) {
+            const double2 s = integral_sum(myJ, sm.tch + (me - 1), 32, Kc);
+            eq = beta0 * fabs(h) / r * sqrt(s.x * s.x + s.y * s.y);
+        }
+        const double budget = STEP_SAFETY * 0.5 * H.tol * tq / H.t_end;
+        const bool ok = tq > 0.0 && budget >= 2.3e-16 * beta0 && eq <= budget;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok || (remaining <= 0.0));
+        if (mask) {
+            pick = __ffs(mask) - 1;
+            tau = __shfl_sync(0xffffffffu, tq, pick);
+        } else {
+            tau_top *= pow(LADDER, 32.0);
+        }
+    }
+    if (lane == 0) {
+        ctl->tau_ok[k] = (pick < 0) ? -1.0 : tau;
+        if (pick < 0) ctl->hd.err = KRY_ETOL;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_exp_apply_b(ExpArgsB ea)
+{
+    KryCtlB *ctl = ea.ctl;
+    KryHdrB &H = ctl->hd;
+    if (H.done) return;
+    const int k = blockIdx.x, lane = threadIdx.x;
+    if (H.err) {
+        if (k == 0 && lane == 0) H.done = 1;
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ExpSmem &sm = *(ExpSmem *)smem_raw;
+    double tau = 1e300;
+    for (int kk = lane; kk < ea.K; kk += 32) tau = fmin(tau, ctl->tau_ok[kk]);
+    for (int o = 16; o > 0; o >>= 1) tau = fmin(tau, __shfl_xor_sync(0xffffffffu, tau, o));
+    const int me = ctl->m_eff[k];
+    load_tridiag_b(sm, ctl, k, me, ea);
+    const double beta0 = ctl->beta0[k], h = sm.be[me - 1];
+    const double t_now = H.t_now, t_end = H.t_end, remaining = t_end - t_now;
+    const bool last = (tau >= remaining);
+    double2 cr = gershgorin(sm, me);
+    const int Kc = cheb_degree(tau * cr.y);
+    cr = chebyshev_basis(sm, me, Kc);
+    const double c = cr.x, r = cr.y;
+    double *myJ = sm.jb + lane * (KMAX + 2);
+    bessel_seq(tau * r, Kc, myJ);
+    if (lane < me) {
+        const double2 s = jacobi_anger_sum(myJ, sm.tch + lane, 32, Kc);
+        double sn, cs;
+        sincos(tau * c, &sn, &cs);
+        const double2 y = cmul(make_double2(cs, -sn), s);
+        const double f = -beta0 * ctl->sigma[lane][k];
+        ctl->coefY[lane][k] = make_double2(f * y.x, f * y.y);
+    } else if (lane < MMAX) {
+        ctl->coefY[lane][k] = make_double2(0.0, 0.0);
+    }
+    if (lane == 0) {
+        double e = 0.0;
+        if (h != 0.0) {
+            const double2 s = integral_sum(myJ, sm.tch + (me - 1), 32, Kc);
+            e = beta0 * fabs(h) / r * sqrt(s.x * s.x + s.y * s.y);
+        }
+        ctl->err_k[k] = e;
+    }
+    for (int kk = lane; kk <= Kc; kk += 32) {
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < me; ++j) {
+            const double t = sm.tch[kk * 32 + j];
+            re += sm.g[j].x * t;
+            im += sm.g[j].y * t;
+        }
+        sm.gk[kk] = make_double2(re, im);
+    }
+    __syncwarp();
+    int next = H.next_out;
+    const int n_times = H.n_times;
+    while (next < n_times) {
+        const int o = next + lane;
+        double tp = 0.0;
+        bool in = false;
+        if (o < n_times) {
+            tp = ea.times[o] - t_now;
+            in = last ? true : (tp <= tau * (1.0 + 1e-12));
+            if (tp < 0.0) tp = 0.0;
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, in);
+        const int cnt = __popc(mk & ~(mk + 1u));
+        if (lane < cnt) {
+            bessel_seq(tp * r, Kc, myJ);
+            double re = 0.0, im = 0.0;
+            for (int kk = 0; kk <= Kc; ++kk) {
+                const double t = myJ[kk] * (kk == 0 ? 1.0 : 2.0);
+                const double2 G = sm.gk[kk];
+                switch (kk & 3) {
+                case 0: re += t * G.x; im += t * G.y; break;
+                case 1: re += t * G.y; im -= t * G.x; break;
+                case 2: re -= t * G.x; im -= t * G.y; break;
+                default: re -= t * G.y; im += t * G.x; break;
+                }
+            }
+            double sn, cs;
+            sincos(tp * c, &sn, &cs);
+            const double2 A = cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
+            ea.P[(size_t)o * ea.K + k] = A.x * A.x + A.y * A.y;
+        }
+        next += cnt;
+        if (cnt < 32) break;
+    }
+    if (k == 0 && lane == 0) {
+        H.next_out_new = next;
+        H.t_next = last ? t_end : t_now + tau;
+        H.finishing = (next >= n_times) ? 1 : 0;
+    }
+}
+
+int launch_exp_b(const ExpArgsB &a, cudaStream_t s)
+{
+    KRY_CU(cudaFuncSetAttribute(k_exp_scan_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ExpSmem)));
+    KRY_CU(cudaFuncSetAttribute(k_exp_apply_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ExpSmem)));
+    k_exp_scan_b<<<a.K, 32, sizeof(ExpSmem), s>>>(a);
+    KRY_CU(cudaGetLastError());
+    k_exp_apply_b<<<a.K, 32, sizeof(ExpSmem), s>>>(a);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
 int launch_smallexp(const ExpArgs &a, cudaStream_t s)
 {
     KRY_CU(cudaFuncSetAttribute(k_smallexp, cudaFuncAttributeMaxDynamicSharedMemorySize,

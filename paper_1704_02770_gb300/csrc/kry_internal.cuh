@@ -48,7 +48,8 @@ struct DevBasis {
 };
 
 // Hamiltonian parameters for the matrix-free H.v.  The field energy
-// sum_i h_i (n_i - 1/2) of a state is ehlo[position of lo in lolist] + ehhi[hi].
+// sum_i h_{k,i} (n_i - 1/2) of a state in realisation k is
+// ehlo[pos * K + k] + ehhi[hi * K + k], pos = position of lo in lolist.
 struct DevHam {
     const double *ehlo_d, *ehhi_d;
     const float *ehlo_f, *ehhi_f;
@@ -56,7 +57,66 @@ struct DevHam {
     double halfJ;   // J / 2
     int nbonds;     // bonds of the chain (L-1 open, L on a ring with L >= 3)
     int pbc;        // ring bond (L-1, 0) present
+    int K;          // realisations (field rows)
 };
+
+// ---------------------------------------------------------------- batched realisations
+constexpr int KBMAX = 128;   // largest K of one batched evolution
+constexpr int PSB = 36;      // partial-sum slots per (CTA, realisation): dots, then NRM, G
+constexpr int TROWS = 16;    // rows (states) per CTA tile of the batched kernels
+
+// Control block of a batched evolution: one Lanczos recurrence per realisation k
+// (structure of arrays, k fastest), one shared time grid and step size.
+struct KryHdrB {   // shared scalars (copied to the host when polling)
+    double t_now, t_end, tol, t_next;
+    double eta_corr, eta_bd;
+    double err_sum, max_orth, vec_passes;
+    double vp_kind[5];
+    unsigned long long n_hv, n_steps, n_corr, n_bd;
+    int K, m, m_run, corr_any, finishing, done, err;
+    int n_times, next_out, next_out_new, r0;
+};
+struct KryCtlB {
+    KryHdrB hd;
+    double alpha[MMAX + 1][KBMAX], beta[MMAX + 1][KBMAX], sigma[MMAX + 2][KBMAX];
+    double2 coefA[MMAX + 1][KBMAX], coefC[MMAX + 1][KBMAX], coefY[MMAX + 1][KBMAX];
+    double2 g[MMAX + 2][KBMAX];
+    double normu2[KBMAX], beta0[KBMAX], tau_ok[KBMAX], err_k[KBMAX], orth[KBMAX];
+    int m_eff[KBMAX], corr[KBMAX];
+};
+
+template <class V>
+struct EvArgsB {
+    DevBasis b;
+    DevHam h;
+    V *W;            // Krylov vectors, element (r, k) of W_i at i*ldW + r*K + k
+    size_t ldW;
+    V *U;
+    const V *G;      // psi0 of a general initial state, or nullptr
+    double2 *part;   // partials [grid][PSB][Kp]
+    KryCtlB *ctl;
+    int K, Kp;       // realisations; Kp = K rounded up to a power of two >= 32
+    int rl_smem;
+};
+
+struct ExpArgsB {
+    KryCtlB *ctl;
+    const double *times;
+    double *P;       // [n_times][K]
+    const void *W;
+    size_t ldW;
+    int c64, K;
+};
+
+template <class V> int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream_t s);
+int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, int mode, int jj,
+                    int general, double es_bytes_per_vec, cudaStream_t s);
+template <class V> int batched_grid(const DevBasis &b, int Kp, int rl_smem);
+int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
+                   int rl_smem, cudaStream_t s);
+int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t s);
+int launch_exp_b(const ExpArgsB &a, cudaStream_t s);
 
 // Device control block of one evolution: Lanczos coefficients of the current Krylov
 // step, time-stepping state and counters.  Written only by single-thread epilogues.

@@ -1,0 +1,112 @@
+"""Batched realisations ([state][K] interleaved, one H.v / Lanczos pass for all K) against
+single runs and the oracle.
+
+Bars: complex128 |dP| <= 1e-10 against the oracle, complex64 <= 1e-5; a batch of K equal
+copies reproduces the single run to 1e-12 (same arithmetic, different reduction order).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import basis as ob
+from oracle import krylov
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(L, hh, seed, K):
+    return np.array([workloads.quasiperiodic_field(L, hh, p) for p in workloads.phases(seed, K)])
+
+
+@pytest.mark.parametrize("K,dtype", [(3, torch.complex128), (64, torch.complex64), (40, torch.complex128),
+                                     (100, torch.complex64)])
+def test_apply_batched_vs_oracle(kry, K, dtype):
+    L, N = 12, 6
+    h = _fields(L, 2.0, 7, K)
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, 1.0, 0.8, h)
+    g = torch.Generator().manual_seed(K)
+    x = torch.randn(B.dim, K, dtype=torch.complex128, generator=g)
+    y = H.apply(x.to(dtype).cuda().contiguous()).cpu().numpy().astype(np.complex128).reshape(B.dim, K)
+    xn = x.to(dtype).numpy().astype(np.complex128)
+    tol = 1e-13 if dtype == torch.complex128 else 2e-6
+    for k in (0, K // 2, K - 1):
+        yo = ob.CSR(L, N, 1.0, 0.8, h[k], True).matvec(np.ascontiguousarray(xn[:, k]))
+        assert np.max(np.abs(y[:, k] - yo)) <= tol * np.max(np.abs(yo))
+
+
+def test_identical_copies_equal_single_run(kry):
+    c = workloads.config("L16_fp64")
+    L, N, h = c["L"], c["n_up"], np.array(c["h"][0])
+    B = kry.Basis(L, N)
+    times = c["times"][:30]
+    P1, _ = kry.Hamiltonian(B, 1.0, 1.0, h).return_probability(c["state"], times, tol=1e-10)
+    PK, st = kry.Hamiltonian(B, 1.0, 1.0, np.tile(h, (5, 1))).return_probability(c["state"], times, tol=1e-10)
+    assert PK.shape == (len(times), 5)
+    for k in range(5):
+        assert np.max(np.abs(PK[:, k] - P1)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,bar", [("c128", 1e-10), ("c64", 1e-5)])
+def test_each_realisation_matches_oracle(kry, dtype, bar):
+    L, N, K = 14, 7, 6
+    h = _fields(L, 1.5, 3, K)
+    times = workloads.log_times(20, 0.1, 60.0)
+    st = workloads.neel_state(L)
+    B = kry.Basis(L, N)
+    P, _ = kry.Hamiltonian(B, 1.0, 1.0, h).return_probability(
+        st, times, tol=1e-10 if dtype == "c128" else 1e-7, dtype=dtype)
+    worst = 0.0
+    for k in range(K):
+        Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
+        Po, _ = krylov.return_probability(Hc, ob.lookup(Hc.basis, st), times, m=30, tol=1e-12)
+        worst = max(worst, float(np.max(np.abs(P[:, k] - Po))))
+    print(f"[parity] batched L14 K=6 {dtype}: max|dP| = {worst:.3e}")
+    assert worst <= bar
+
+
+def test_general_initial_states_batched(kry):
+    L, N, K = 10, 5, 4
+    h = _fields(L, 1.0, 9, K)
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, 1.0, 1.0, h)
+    rng = np.random.default_rng(2)
+    psi0 = rng.normal(size=(B.dim, K)) + 1j * rng.normal(size=(B.dim, K))
+    psi0 /= np.linalg.norm(psi0, axis=0)
+    times = [0.0, 0.4, 3.0]
+    x = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
+    out = torch.empty_like(x)
+    P, _ = H.evolve(x, times, tol=1e-10, psi_out=out)
+    out = out.cpu().numpy()
+    for k in range(K):
+        Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
+        Po, psio, _ = krylov.evolve(Hc.matvec, Hc.norm_inf(), psi0[:, k].copy(), times, m=30, tol=1e-12)
+        assert np.max(np.abs(P[:, k] - Po)) <= 1e-10
+        assert np.linalg.norm(out[:, k] - psio) <= 1e-10
+
+
+def test_config_L22_batched_full_size(kry):
+    """K = 64 phases at L = 22 (D = 705,432), complex64: two realisations against the oracle
+    over the first output times; all 64 against complex128 batched over t <= 1."""
+    c = workloads.config("L22_batched_h1.5")
+    L, N, K = c["L"], c["n_up"], 64
+    h = np.array(c["h"])
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, 1.0, 1.0, h)
+    times = c["times"]
+    P64, st = H.return_probability(c["state"], times, tol=1e-7, dtype="c64")
+    assert P64.shape == (40, K)
+    assert np.all(P64 >= -1e-6) and np.all(P64 <= 1 + 1e-6)
+    k6 = 6
+    for k in (0, K - 1):
+        Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
+        Po, _ = krylov.return_probability(Hc, ob.lookup(Hc.basis, c["state"]), times[:k6], m=30, tol=1e-12)
+        err = float(np.max(np.abs(P64[:k6, k] - Po)))
+        print(f"[parity] L22 K=64 c64 realisation {k} (t <= {times[k6 - 1]:.3f}): max|dP| = {err:.3e}")
+        assert err <= 1e-5
+    n1 = sum(1 for t in times if t <= 1.0)
+    P128, _ = H.return_probability(c["state"], times[:n1], tol=1e-10, dtype="c128")
+    err = float(np.max(np.abs(P128 - P64[:n1])))
+    print(f"[parity] L22 K=64 c64 vs c128 (t <= 1): max|dP| = {err:.3e}")
+    assert err <= 1e-5
