@@ -40,13 +40,14 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--form", default="c128", choices=["c128", "c64"],
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs): for ncu captures")
     a = ap.parse_args()
     if a.kernels_only:
-        a.no_mixed = a.no_cpu_baseline = True
+        a.no_mixed = a.no_cpu_baseline = a.no_batched = True
     return a
 
 
@@ -240,14 +241,17 @@ def run_ours(args):
     D = B.dim
     stream = torch.cuda.current_stream()
 
-    def evolve(dtype, tol):
-        return H.return_probability(c["state"], times, m=c["m"], tol=tol, dtype=dtype)
+    def timed(dtype, tol, profile, Hx=None, cx=None):
+        Hx = H if Hx is None else Hx
+        cx = c if cx is None else cx
 
-    def timed(dtype, tol, profile):
+        def evolve(dt, tl):
+            return Hx.return_probability(cx["state"], cx["times"], m=cx["m"], tol=tl, dtype=dt)
+
         for _ in range(args.warmup):
             evolve(dtype, tol)
         if profile:
-            H.profile(True)
+            Hx.profile(True)
         barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -261,8 +265,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
-        prof = H.profile_read() if profile else None
-        H.profile(False)
+        prof = Hx.profile_read() if profile else None
+        Hx.profile(False)
         return e0.elapsed_time(e1) / 1e3, hv, launches, P, st, prof
 
     form = args.form if args.kernels_only else "c128"
@@ -298,6 +302,25 @@ def run_ours(args):
                         "max_abs_dP_vs_fp64": float(np.max(np.abs(P64 - P128))),
                         "tol": 1e-7, "roofline": roofline(prof64, "c64", D, c, L, N, clocks)}
         out["gpu_launches"] += l64
+    # batched realisations: the K = 64 phase ensemble of L = 22 in one interleaved launch
+    if not args.no_batched:
+        cb = workloads.config("L22_batched_h1.5")
+        Bb = kry.Basis(cb["L"], cb["n_up"])
+        Hb = kry.Hamiltonian(Bb, cb["J"], cb["Delta"], cb["h"], pbc=cb["pbc"])
+        Kb = Hb.K
+        secb, hvb, lb, Pb, stb, profb = timed("c64", 1e-7, profile=True, Hx=Hb, cx=cb)
+        ub, sb = aggregate(Bb.dim * Kb * hvb, secb, world)
+        out["batched"] = {
+            "workload": f"L22_batched_h1.5: L=22 N_up=11 D={Bb.dim} K={Kb} phases, h=1.5, "
+                        "40 log times in [0.1,100], tol 1e-7",
+            "dtype": "c64 vectors [D][K] interleaved, fp64 coefficients",
+            "value": ub / sb, "unit": "state-updates/s (D x K x H.v / s)",
+            "ms_per_step": 1e3 * sb / args.steps, "krylov_steps_per_step": stb["n_krylov_steps"],
+            "speedup_vs_fp64": (ub / sb) / value,
+            "disorder_avg_P_last": float(np.mean(Pb[-1])),
+            "roofline": roofline(profb, "c64", Bb.dim * Kb, cb, cb["L"], cb["n_up"], clocks)}
+        out["gpu_launches"] += lb
+        del Hb, Bb
     out["config"] = cfg
     if args.kernels_only:
         if rank == 0:
