@@ -118,6 +118,21 @@ int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const doub
                            int n_times, int m, double tol, double *P_out,
                            kry_stats *stats, void *stream);
 
+/* Gradient of the return probability of Eq. SP with respect to the on-site fields and to
+ * Delta, for psi0 = the basis state psi0_state and one time t >= 0 (a single-realisation
+ * Hamiltonian, K = 1; complex128).  With psi(s) = exp(-iHs) psi0 and the costate
+ * lambda(s) = exp(+iH(t-s)) psi0:
+ *   dA/dtheta = -i int_0^t <lambda(s)| dH/dtheta |psi(s)> ds,  dP/dtheta = 2 Re(conj(A) dA/dtheta),
+ *   dH/dh_i = Sz_i,  dH/dDelta = J sum_b Sz Sz.
+ * The costate is evolved backward with the same Krylov kernels (a forward evolution
+ * under -H); psi is checkpointed after every ckpt_every-th Krylov step of the forward
+ * sweep and recomputed interval by interval during the backward sweep; the integral uses
+ * composite 16-point Gauss-Legendre rules.  Outputs (host): P = P(t), dP_dh[L],
+ * dP_dDelta.  Allocates its own temporary device buffers (a few vectors of D complex128
+ * plus at most 64 checkpoints); synchronises `stream`.  m, tol: as kry_evolve. */
+int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double tol, int ckpt_every,
+             double *P, double *dP_dh, double *dP_dDelta, kry_stats *stats, void *stream);
+
 /* Small-exponential kernel exposed for testing (Sec. 2: psi ~ V_m exp(-itA_m) e_1).
  * Given the symmetric tridiagonal T (alpha[m] diagonal, beta[m-1] off-diagonal, host
  * arrays), its coupling h to the next Krylov vector, and tau >= 0, computes on the

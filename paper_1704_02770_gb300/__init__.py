@@ -46,6 +46,7 @@ SIGNATURES = {
     "kry_evolve": (_i, [_vp, _i, _vp, _dp, _i, _i, _d, _vp, _dp, ctypes.POINTER(Stats), _vp]),
     "kry_return_probability": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp,
                                     ctypes.POINTER(Stats), _vp]),
+    "kry_grad": (_i, [_vp, ctypes.c_uint64, _d, _i, _d, _i, _dp, _dp, _dp, ctypes.POINTER(Stats), _vp]),
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_workspace_size": (_i64, [_vp, _i, _i]),
@@ -192,6 +193,19 @@ class Hamiltonian:
                                              P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
 
+    def grad(self, state: int, t: float, m: int = 30, tol: float = 1e-10, ckpt_every: int = 8,
+             stream=None):
+        """P(t) and its gradient: returns (P, dP/dh [L], dP/dDelta, stats)."""
+        import numpy as np
+        P = np.zeros(1)
+        gh = np.zeros(self.basis.L)
+        gd = np.zeros(1)
+        st = Stats()
+        _check(load().kry_grad(self._h, ctypes.c_uint64(state), float(t), m, tol, ckpt_every,
+                               P.ctypes.data_as(_dp), gh.ctypes.data_as(_dp), gd.ctypes.data_as(_dp),
+                               ctypes.byref(st), _stream(stream)))
+        return float(P[0]), gh, float(gd[0]), st.as_dict()
+
     def profile(self, on: bool = True):
         """Turn per-kernel CUDA-event profiling of later evolutions on or off (resets it)."""
         _check(load().kry_profile_enable(self._h, 1 if on else 0))
@@ -231,3 +245,33 @@ def tridiag_expv(alpha, beta, h: float, tau: float, stream=None):
     _check(load().kry_tridiag_expv(ap, bp, a.size, float(h), float(tau), y.ctypes.data_as(_dp),
                                    err.ctypes.data_as(_dp), _stream(stream)))
     return y[0::2] + 1j * y[1::2], float(err[0])
+
+
+def _return_probability_fn():
+    import torch
+
+    class ReturnProbability(torch.autograd.Function):
+        """P(t) = |<psi0| exp(-iHt) |psi0>|^2 as a differentiable function of the on-site
+        fields h [L] and of Delta (float64 CPU tensors).  Forward and backward both run
+        kry_grad on the GPU: the backward pass returns grad_output * dP/dh and
+        grad_output * dP/dDelta computed by the adjoint (costate) evolution."""
+
+        @staticmethod
+        def forward(ctx, h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every):
+            H = Hamiltonian(basis, float(J), float(Delta.item()), h.detach().cpu().numpy(), pbc=pbc)
+            P, gh, gd, _ = H.grad(state, t, m=m, tol=tol, ckpt_every=ckpt_every)
+            H.close()
+            ctx.save_for_backward(torch.from_numpy(gh), torch.tensor(gd, dtype=torch.float64))
+            return torch.tensor(P, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            gh, gd = ctx.saved_tensors
+            return g * gh, g * gd, None, None, None, None, None, None, None, None
+
+    return ReturnProbability
+
+
+def return_probability(h, Delta, basis, J, state, t, pbc=True, m=30, tol=1e-10, ckpt_every=8):
+    """Differentiable P(t): h a float64 tensor [L], Delta a float64 scalar tensor."""
+    return _return_probability_fn().apply(h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every)

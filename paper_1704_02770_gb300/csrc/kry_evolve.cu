@@ -37,7 +37,7 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int rl_in_smem(const DevBasis &b) { return b.Llo <= 15 ? 1 : 0; }
 
 struct Layout {
-    size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, bytes;
+    size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, oY, bytes;
 };
 
 Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
@@ -53,9 +53,22 @@ Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
     l.oCtl = round_up(l.oPart + (size_t)grid * PSTRIDE * sizeof(double2), 256);
     l.oTimes = round_up(l.oCtl + sizeof(KryCtl), 256);
     l.oP = round_up(l.oTimes + sizeof(double) * (size_t)n_times, 256);
-    l.bytes = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    l.oY = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    l.bytes = round_up(l.oY + sizeof(double2) * MMAX * (size_t)n_times, 256);
     return l;
 }
+
+// Optional outputs of an evolution used by the gradient: whole vectors at every output
+// time, and checkpoints of psi after every `ckpt_every`-th Krylov step.
+struct EvOpts {
+    void *vec_out = nullptr;   // [n_times][ldOut] elements
+    size_t ldOut = 0;
+    void *ckpt = nullptr;      // [ckpt_cap][ldC] elements
+    size_t ldC = 0;
+    int ckpt_every = 0, ckpt_cap = 0;
+    int n_ckpt = 0;            // out
+    double ckpt_t[64] = {};    // out
+};
 
 int grid_for(const kry_ham_s *H, int dtype)
 {
@@ -79,7 +92,8 @@ int kind_of(int k, int m)
 }
 
 template <class V>
-int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int grid)
+int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int grid,
+                 const EvOpts *opt)
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
@@ -107,8 +121,21 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     }
     mark();
     if (rc == KRY_OK) rc = launch_smallexp(ea, cs);
+    if (rc == KRY_OK && opt && opt->vec_out) {
+        VecOutArgs<V> va{};
+        va.W = a.W;
+        va.ldW = a.ldW;
+        va.Yout = ea.Yout;
+        va.out = (V *)opt->vec_out;
+        va.ldOut = opt->ldOut;
+        va.ctl = a.ctl;
+        va.D = a.b.D;
+        rc = launch_vecout<V>(va, grid, cs);
+    }
     mark();
     if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, grid, cs);
+    if (rc == KRY_OK && opt && opt->ckpt)
+        rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, grid, cs);
     mark();
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -122,7 +149,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
 template <class V>
 int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool general,
              const double *times, int n_times, int m, double tol, void *d_psi_out, double *P_out,
-             kry_stats *st, cudaStream_t s)
+             kry_stats *st, cudaStream_t s, EvOpts *opt = nullptr)
 {
     const DevBasis &b = H->b->dev;
     const int grid = grid_for(H, dtype);
@@ -157,15 +184,22 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     ea.W = a.W;
     ea.ldW = l.ldW;
     ea.c64 = dtype == KRY_C64;
+    ea.Yout = (opt && opt->vec_out) ? (double2 *)(base + l.oY) : nullptr;
+    const void *vkey = opt ? opt->vec_out : nullptr, *ckey = opt ? opt->ckpt : nullptr;
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
                      H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
-                     H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on))
+                     H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
+                     H->g_vec != vkey || H->g_ck != ckey ||
+                     (opt && (H->g_ldo != opt->ldOut || H->g_ldc != opt->ldC))))
         drop_graph(H);
     if (!H->gexec) {
-        if (int rc = capture_step<V>(H, a, ea, m, grid)) return rc;
+        if (int rc = capture_step<V>(H, a, ea, m, grid, opt)) return rc;
         H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid;
         H->g_ws = H->ws; H->g_G = base + l.oP;
+        H->g_vec = vkey; H->g_ck = ckey;
+        H->g_ldo = opt ? opt->ldOut : 0;
+        H->g_ldc = opt ? opt->ldC : 0;
     }
     cudaEvent_t ev0, ev1;
     KRY_CU(cudaEventCreate(&ev0));
@@ -181,6 +215,10 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     c.n_times = n_times;
     c.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
     c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
+    if (opt && opt->ckpt) {
+        c.ckpt_every = opt->ckpt_every;
+        c.ckpt_cap = std::min(opt->ckpt_cap, 64);
+    }
     const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)H->K;
     if (general) {
         c.r0 = -1;
@@ -261,7 +299,11 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * nk + (general ? 1 : 1);
+        st->n_launches = launched * (nk + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
+    }
+    if (opt && opt->ckpt) {
+        opt->n_ckpt = hp->n_ckpt;
+        for (int i = 0; i < hp->n_ckpt && i < 64; ++i) opt->ckpt_t[i] = hp->ckpt_t[i];
     }
     return KRY_OK;
 }
@@ -610,4 +652,221 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
     return H->K > 1
                ? evolve_bt<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
                : evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+}
+
+// ---------------------------------------------------------------- adjoint gradient
+//
+// A(t) = <psi0| exp(-iHt) |psi0>, P = |A|^2 (Eq. SP).  For a parameter theta of H,
+//     dA/dtheta = -i int_0^t <lambda(s)| dH/dtheta |psi(s)> ds,
+//     psi(s) = exp(-iHs) psi0,   lambda(s) = exp(+iH(t - s)) psi0   (the costate),
+//     dP/dtheta = 2 Re(conj(A) dA/dtheta),
+// with dH/dh_i = Sz_i and dH/dDelta = J sum_b Sz Sz (both diagonal).  The costate is
+// evolved backward from lambda(t) = psi0 with the same Krylov kernels, as a forward
+// evolution under -H in u = t - s.  psi is checkpointed after every `ckpt_every`-th Krylov
+// step of the forward sweep; the backward sweep visits the checkpoint intervals from the
+// last to the first, recomputes psi from the interval's checkpoint at the quadrature nodes
+// inside it, advances the costate through the same interval, and accumulates the
+// integrand.  The integral uses composite 16-point Gauss-Legendre rules on segments short
+// enough that (spectral width bound) x (segment length) <= 20.
+
+namespace {
+
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    // Newton iteration on the Legendre polynomial P_n from cosine initial guesses
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), p1 = 0.0, p0 = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            p0 = 1.0;
+            p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+void add_stats(kry_stats &a, const kry_stats &b)
+{
+    a.n_hv += b.n_hv;
+    a.n_krylov_steps += b.n_krylov_steps;
+    a.n_second_pass += b.n_second_pass;
+    a.n_breakdowns += b.n_breakdowns;
+    a.err_estimate += b.err_estimate;
+    a.max_orth_loss = std::max(a.max_orth_loss, b.max_orth_loss);
+    a.time_ms += b.time_ms;
+    a.algo_bytes += b.algo_bytes;
+    a.n_launches += b.n_launches;
+}
+
+}  // namespace
+
+extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double tol, int ckpt_every,
+                        double *P, double *dP_dh, double *dP_dDelta, kry_stats *stats, void *stream)
+{
+    if (!H || !P || !dP_dh || !dP_dDelta || !(t >= 0.0) || !std::isfinite(t) || m < 1 || m > MMAX ||
+        !(tol > 0.0) || ckpt_every < 1) {
+        set_error("kry_grad: bad arguments (need H, outputs, t >= 0, 1 <= m <= %d, tol > 0, ckpt_every >= 1)", MMAX);
+        return KRY_EINVAL;
+    }
+    if (H->K != 1) { set_error("kry_grad: one realisation (K = 1) only"); return KRY_EINVAL; }
+    const int L = H->b->L;
+    if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
+        set_error("kry_grad: state is not in the (L=%d, N=%d) sector", L, H->b->N);
+        return KRY_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevBasis &b = H->b->dev;
+    const size_t D = b.D, ldv = round_up(D, 64), vb = ldv * sizeof(double2);
+    uint64_t r0 = 0;
+    {
+        int j = 0;
+        for (int p = 0; p < L; ++p)
+            if ((psi0_state >> p) & 1ull) r0 += binom_host(p, ++j);
+    }
+    kry_stats tot{};
+    if (t == 0.0) {
+        *P = 1.0;
+        for (int i = 0; i < L; ++i) dP_dh[i] = 0.0;
+        *dP_dDelta = 0.0;
+        if (stats) *stats = tot;
+        return KRY_OK;
+    }
+    // quadrature nodes over [0, t]
+    double hsum = 0.0;
+    for (int i = 0; i < L; ++i) hsum += std::fabs(H->h[i]);
+    const int nb = H->dev.nbonds;
+    const double wbound = 2.0 * (0.5 * std::fabs(H->J) * nb + 0.25 * std::fabs(H->J * H->Delta) * nb + 0.5 * hsum);
+    const int nseg = std::max(1, (int)std::ceil(wbound * t / 20.0));
+    std::vector<double> gx, gw, sq, wq;
+    gauss_legendre(16, gx, gw);
+    for (int sgi = 0; sgi < nseg; ++sgi) {
+        const double a0 = t * sgi / nseg, a1 = t * (sgi + 1) / nseg, hh = 0.5 * (a1 - a0);
+        for (int i = 0; i < 16; ++i) {
+            sq.push_back(a0 + hh * (gx[i] + 1.0));
+            wq.push_back(hh * gw[i]);
+        }
+    }
+    const int cap = 64;
+    // device buffers
+    DevBuf bpsi0, bpsit, bck, blamA, blamB, bw, bacc, bpart;
+    KRY_CU(cudaMalloc(&bpsi0.p, vb));
+    KRY_CU(cudaMalloc(&bpsit.p, vb));
+    KRY_CU(cudaMalloc(&blamA.p, vb));
+    KRY_CU(cudaMalloc(&blamB.p, vb));
+    KRY_CU(cudaMalloc(&bw.p, sizeof(double) * wq.size()));
+    KRY_CU(cudaMalloc(&bacc.p, sizeof(double2) * (MMAX + 2) + 64));
+    const int ggrid = (int)std::min<size_t>((D + TILE - 1) / TILE, 152 * 2);
+    KRY_CU(cudaMalloc(&bpart.p, sizeof(double2) * PSTRIDE * (size_t)ggrid));
+    double2 *acc = (double2 *)bacc.p;
+    unsigned *counter = (unsigned *)(acc + MMAX + 2);
+    KRY_CU(cudaMemsetAsync(bacc.p, 0, sizeof(double2) * (MMAX + 2) + 64, s));
+    KRY_CU(cudaMemcpyAsync(bw.p, wq.data(), sizeof(double) * wq.size(), cudaMemcpyHostToDevice, s));
+    KRY_CU(cudaMemsetAsync(bpsi0.p, 0, vb, s));
+    if (int rc = launch_set_basis_state(bpsi0.p, 0, (uint32_t)r0, s)) return rc;
+    // 1. forward sweep with checkpoints
+    size_t ck_bytes = (size_t)cap * vb;
+    KRY_CU(cudaMalloc(&bck.p, ck_bytes));
+    EvOpts fo;
+    fo.ckpt = bck.p;
+    fo.ldC = ldv;
+    fo.ckpt_every = ckpt_every;
+    fo.ckpt_cap = cap;
+    double Pt = 0.0;
+    kry_stats st{};
+    if (int rc = evolve_t<double2>(H, KRY_C128, nullptr, psi0_state, false, &t, 1, m, tol, bpsit.p, &Pt, &st, s, &fo))
+        return rc;
+    add_stats(tot, st);
+    double2 A;
+    KRY_CU(cudaMemcpyAsync(&A, (double2 *)bpsit.p + r0, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    KRY_CU(cudaStreamSynchronize(s));
+    *P = A.x * A.x + A.y * A.y;
+    const int C = fo.n_ckpt;
+    std::vector<double> T(C + 2);
+    T[0] = 0.0;
+    for (int c = 0; c < C; ++c) T[c + 1] = fo.ckpt_t[c];
+    T[C + 1] = t;
+    // node ranges per interval and the largest one
+    std::vector<int> qa(C + 1), qb(C + 1);
+    int nmax = 1;
+    for (int c = 0; c <= C; ++c) {
+        int a = 0;
+        while (a < (int)sq.size() && sq[a] < T[c]) ++a;
+        int e = a;
+        while (e < (int)sq.size() && (sq[e] < T[c + 1] || (c == C && sq[e] <= t))) ++e;
+        qa[c] = a;
+        qb[c] = e;
+        nmax = std::max(nmax, e - a + 1);
+    }
+    DevBuf bP, bL;
+    KRY_CU(cudaMalloc(&bP.p, (size_t)nmax * vb));
+    KRY_CU(cudaMalloc(&bL.p, (size_t)nmax * vb));
+    // 2. costate Hamiltonian -H (J -> -J at fixed Delta flips both bond terms; h -> -h)
+    std::vector<double> hneg(L);
+    for (int i = 0; i < L; ++i) hneg[i] = -H->h[i];
+    kry_ham Hn = nullptr;
+    if (int rc = kry_hamiltonian_set(H->b, -H->J, H->Delta, hneg.data(), 1, H->boundary, &Hn)) return rc;
+    struct HamGuard { kry_ham h; ~HamGuard() { kry_hamiltonian_destroy(h); } } guard{Hn};
+    KRY_CU(cudaMemcpyAsync(blamA.p, bpsi0.p, vb, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> tim, Pd(nmax + 1);
+    for (int c = C; c >= 0; --c) {
+        const int n = qb[c] - qa[c];
+        const double Ta = T[c], Tb = T[c + 1];
+        const void *start = (c == 0) ? bpsi0.p : (const void *)((char *)bck.p + (size_t)(c - 1) * vb);
+        if (n > 0) {
+            // 3a. psi at the nodes of the interval, recomputed from its checkpoint
+            tim.clear();
+            for (int q = qa[c]; q < qb[c]; ++q) tim.push_back(std::max(0.0, sq[q] - Ta));
+            EvOpts po;
+            po.vec_out = bP.p;
+            po.ldOut = ldv;
+            if (int rc = evolve_t<double2>(H, KRY_C128, start, 0, true, tim.data(), n, m, tol, nullptr, Pd.data(), &st, s, &po))
+                return rc;
+            add_stats(tot, st);
+        }
+        // 3b. costate through the same interval: u from t - Tb to t - Ta, outputs at u = t - s_q
+        tim.clear();
+        for (int q = qb[c] - 1; q >= qa[c]; --q) tim.push_back(std::max(0.0, (t - sq[q]) - (t - Tb)));
+        tim.push_back(Tb - Ta);
+        EvOpts lo;
+        lo.vec_out = bL.p;
+        lo.ldOut = ldv;
+        if (int rc = evolve_t<double2>(Hn, KRY_C128, blamA.p, 0, true, tim.data(), (int)tim.size(), m, tol, blamB.p, Pd.data(), &st, s, &lo))
+            return rc;
+        add_stats(tot, st);
+        std::swap(blamA.p, blamB.p);
+        // 3c. integrand at the interval's nodes
+        if (n > 0) {
+            if (int rc = launch_grad_acc(b, H->dev, H->J, (const double2 *)bP.p, (const double2 *)bL.p, ldv,
+                                         (const double *)bw.p + qa[c], n, (double2 *)bpart.p, acc, counter, ggrid, s))
+                return rc;
+        }
+    }
+    std::vector<double2> hacc(L + 1);
+    KRY_CU(cudaMemcpyAsync(hacc.data(), acc, sizeof(double2) * (L + 1), cudaMemcpyDeviceToHost, s));
+    KRY_CU(cudaStreamSynchronize(s));
+    // dA = -i acc; dP = 2 Re(conj(A) dA) = 2 (A.x acc.y - A.y acc.x)
+    for (int i = 0; i <= L; ++i) {
+        const double dA_re = hacc[i].y, dA_im = -hacc[i].x;
+        const double dp = 2.0 * (A.x * dA_re + A.y * dA_im);
+        if (i < L) dP_dh[i] = dp;
+        else *dP_dDelta = dp;
+    }
+    if (stats) *stats = tot;
+    return KRY_OK;
 }

@@ -289,10 +289,29 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
             const double2 A = cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
             ea.P[o] = A.x * A.x + A.y * A.y;
         }
+        if (ea.Yout) {
+            // whole-vector dense output: psi(t_o) = sum_j Yout[o][j] W_j with
+            // Yout[o][j] = beta sigma_j [exp(-i tau' T) e_1]_j, from the same Bessel rows
+            __syncwarp();
+            for (int bq = 0; bq < cnt; ++bq) {
+                const double tpb = __shfl_sync(0xffffffffu, tp, bq);
+                if (lane < me) {
+                    const double2 s = jacobi_anger_sum(sm.jb + bq * (KMAX + 2), sm.tch + lane, 32, K);
+                    double sn, cs;
+                    sincos(tpb * c, &sn, &cs);
+                    const double2 y = cmul(make_double2(cs, -sn), s);
+                    const double f = beta0 * ctl->sigma[lane];
+                    ea.Yout[(size_t)(next + bq) * MMAX + lane] = make_double2(f * y.x, f * y.y);
+                }
+            }
+            __syncwarp();
+        }
         next += cnt;
         if (cnt < 32) break;
     }
     if (lane == 0) {
+        ctl->out_begin = ctl->next_out;
+        ctl->out_end = next;
         ctl->next_out = next;
         ctl->t_now = last ? t_end : t_now + tau;
         ctl->tau_prev = tau;

@@ -49,13 +49,14 @@ __global__ void __launch_bounds__(NTHR) k_apply(DevBasis b, DevHam hm, const V *
 // Write this CTA's partials, then let the last CTA sum all partials (CTA order) into
 // fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).
 __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *part, KryCtl *ctl,
-                                                double2 *fin, int *flag)
+                                                double2 *fin, int *flag, unsigned *counter = nullptr)
 {
     const int tid = threadIdx.x;
+    if (!counter) counter = &ctl->counter;
     if (tid < PSTRIDE) part[(size_t)blockIdx.x * PSTRIDE + tid] = red[tid];
     __threadfence();
     __syncthreads();
-    if (tid == 0) *flag = (atomicAdd(&ctl->counter, 1u) == gridDim.x - 1) ? 1 : 0;
+    if (tid == 0) *flag = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1 : 0;
     __syncthreads();
     if (!*flag) return false;
     __threadfence();
@@ -312,6 +313,120 @@ __global__ void k_set_basis_state(V *W0, uint32_t r0)
     W0[r0] = one;
 }
 
+// ---------------------------------------------------------------- dense vector output
+
+// psi(t_o) = sum_j Yout[o][j] W_j for every output time o inside the current step (the
+// small exponential fills Yout and [out_begin, out_end)); runs before the combine
+// overwrites W_0.
+template <class V>
+__global__ void __launch_bounds__(NTHR) k_vecout(VecOutArgs<V> a)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done) return;
+    const int ob = ctl->out_begin, oe = ctl->out_end, me = ctl->m_eff;
+    if (ob >= oe) return;
+    __shared__ V cf[MMAX];
+    for (int o = ob; o < oe; ++o) {
+        __syncthreads();
+        if (threadIdx.x < me) cf[threadIdx.x] = VT<V>::from(a.Yout[(size_t)o * MMAX + threadIdx.x]);
+        __syncthreads();
+        V *out = a.out + (size_t)o * a.ldOut;
+        for (size_t r = (size_t)blockIdx.x * NTHR + threadIdx.x; r < a.D; r += (size_t)gridDim.x * NTHR) {
+            V w = VT<V>::zero();
+            for (int j = 0; j < me; ++j) {
+                const V v = a.W[(size_t)j * a.ldW + r];
+                const V c = cf[j];
+                w.x += c.x * v.x - c.y * v.y;
+                w.y += c.x * v.y + c.y * v.x;
+            }
+            out[r] = w;
+        }
+    }
+}
+
+// Copy psi (= W_0 after the combine) into checkpoint slot n_steps/every - 1 after every
+// `every`-th Krylov step, and record its time.
+template <class V>
+__global__ void __launch_bounds__(NTHR) k_ckpt(const V *__restrict__ W0, V *__restrict__ ck, size_t ldC,
+                                               KryCtl *ctl, uint32_t D)
+{
+    if (ctl->done || ctl->ckpt_every <= 0) return;
+    const long long ns = ctl->n_steps;
+    if (ns % ctl->ckpt_every != 0) return;
+    const long long slot = ns / ctl->ckpt_every - 1;
+    if (slot < 0 || slot >= ctl->ckpt_cap) return;
+    V *dst = ck + (size_t)slot * ldC;
+    for (size_t r = (size_t)blockIdx.x * NTHR + threadIdx.x; r < D; r += (size_t)gridDim.x * NTHR) dst[r] = W0[r];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->ckpt_t[slot] = ctl->t_now;
+        ctl->n_ckpt = (int)slot + 1;
+    }
+}
+
+// ---------------------------------------------------------------- gradient integrand
+
+__global__ void __launch_bounds__(NTHR) k_grad_acc(DevBasis b, DevHam hm, double J, const double2 *__restrict__ psi,
+                                                   const double2 *__restrict__ lam, size_t ld,
+                                                   const double *__restrict__ w, int nq, double2 *part,
+                                                   double2 *acc_out, unsigned *counter)
+{
+    __shared__ uint32_t koff_s[20], bsz_s[20];
+    __shared__ double2 red[PSTRIDE];
+    __shared__ double2 wtmp[NTHR / 32];
+    __shared__ int flag;
+    const int tid = threadIdx.x, L = b.L;
+    stage_tables(b, koff_s, bsz_s, nullptr, 0);
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    __syncthreads();
+    double2 acc[MMAX + 1];
+#pragma unroll
+    for (int i = 0; i <= MMAX; ++i) acc[i] = make_double2(0.0, 0.0);
+    const uint32_t D = b.D, ntiles = (D + TILE - 1) / TILE;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const double czz = 0.25 * J;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r = tile * TILE + tid;
+        if (r >= D) continue;
+        uint32_t hi, off;
+        int klo;
+        tile_unrank(b, bsz_s, tile * TILE, tid, hi, off, klo);
+        const uint32_t s = (hi << b.Llo) | __ldg(b.lolist + koff_s[klo] + off);
+        double2 S = make_double2(0.0, 0.0);
+        for (int q = 0; q < nq; ++q) {
+            const double2 l = __ldg(lam + (size_t)(nq - 1 - q) * ld + r), p = __ldg(psi + (size_t)q * ld + r);
+            const double wq = __ldg(w + q);
+            S.x += wq * (l.x * p.x + l.y * p.y);
+            S.y += wq * (l.x * p.y - l.y * p.x);
+        }
+#pragma unroll
+        for (int i = 0; i < MMAX; ++i) {
+            if (i < L) {
+                const double z = ((s >> i) & 1u) ? 0.5 : -0.5;
+                acc[i].x += z * S.x;
+                acc[i].y += z * S.y;
+            }
+        }
+        const int nanti = __popc((s ^ (s >> 1)) & obc) + (hm.pbc ? (int)((s ^ (s >> (L - 1))) & 1u) : 0);
+        const double zz = czz * (double)(hm.nbonds - 2 * nanti);
+        acc[MMAX].x += zz * S.x;
+        acc[MMAX].y += zz * S.y;
+    }
+#pragma unroll
+    for (int i = 0; i <= MMAX; ++i) {
+        if (i < L || i == MMAX) cta_sum_into(acc[i], red, i, wtmp);
+    }
+    double2 *fin = red;
+    if (!finish_partials(red, part, nullptr, fin, &flag, counter)) return;
+    if (tid < L) {
+        acc_out[tid].x += fin[tid].x;
+        acc_out[tid].y += fin[tid].y;
+    } else if (tid == L) {
+        acc_out[L].x += fin[MMAX].x;
+        acc_out[L].y += fin[MMAX].y;
+    }
+    if (tid == 0) *counter = 0;
+}
+
 // ---------------------------------------------------------------- launchers
 
 size_t apply_smem(const DevBasis &b, int rl_smem, int)
@@ -405,6 +520,35 @@ int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s)
     return KRY_OK;
 }
 
+template <class V>
+int launch_vecout(const VecOutArgs<V> &a, int grid, cudaStream_t s)
+{
+    k_vecout<V><<<grid, NTHR, 0, s>>>(a);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template <class V>
+int launch_ckpt(const V *W0, V *ckpt, size_t ldC, KryCtl *ctl, uint32_t D, int grid, cudaStream_t s)
+{
+    k_ckpt<V><<<grid, NTHR, 0, s>>>(W0, ckpt, ldC, ctl, D);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+int launch_grad_acc(const DevBasis &b, const DevHam &h, double J, const double2 *psi, const double2 *lam,
+                    size_t ld, const double *w, int nq, double2 *part, double2 *acc, unsigned *counter,
+                    int grid, cudaStream_t s)
+{
+    k_grad_acc<<<grid, NTHR, 0, s>>>(b, h, J, psi, lam, ld, w, nq, part, acc, counter);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template int launch_vecout<double2>(const VecOutArgs<double2> &, int, cudaStream_t);
+template int launch_vecout<float2>(const VecOutArgs<float2> &, int, cudaStream_t);
+template int launch_ckpt<double2>(const double2 *, double2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
+template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template int vector_grid<double2>(const DevBasis &, int);
 template int vector_grid<float2>(const DevBasis &, int);
 template int launch_passA<double2>(const EvArgs<double2> &, int, int, cudaStream_t);

@@ -136,7 +136,31 @@ struct KryCtl {
     int m, m_eff, corr, finishing, done, err;
     int n_times, next_out, r0;
     unsigned int counter;      // ticket of the last-CTA reductions
+    // dense vector output (outputs [out_begin, out_end) of the current step) and checkpoints
+    int out_begin, out_end;
+    int ckpt_every, n_ckpt, ckpt_cap;
+    double ckpt_t[64];
 };
+
+// Dense output of whole vectors: psi(t_o) = sum_j Yout[o][j] W_j, written to out + o * ldOut.
+template <class V>
+struct VecOutArgs {
+    const V *W;
+    size_t ldW;
+    const double2 *Yout;       // [n_times][MMAX]
+    V *out;
+    size_t ldOut;
+    KryCtl *ctl;
+    uint32_t D;
+};
+template <class V> int launch_vecout(const VecOutArgs<V> &a, int grid, cudaStream_t s);
+template <class V> int launch_ckpt(const V *W0, V *ckpt, size_t ldC, KryCtl *ctl, uint32_t D, int grid,
+                                   cudaStream_t s);
+// Gradient integrand: acc[i] += sum_q w_q sum_r conj(lam_{nq-1-q}[r]) psi_q[r] dH_i[r] over the L
+// single-site Sz_i (i < L) and the bond sum J/4 (nbonds - 2 n_anti) (i = L).
+int launch_grad_acc(const DevBasis &b, const DevHam &h, double J, const double2 *psi, const double2 *lam,
+                    size_t ld, const double *w, int nq, double2 *part, double2 *acc, unsigned *counter,
+                    int grid, cudaStream_t s);
 
 template <class V>
 struct EvArgs {
@@ -158,6 +182,7 @@ struct ExpArgs {
     const void *W;   // Krylov vectors (element type given by c64)
     size_t ldW;
     int c64;
+    double2 *Yout;   // nullable: combine coefficients of every output time [n_times][MMAX]
 };
 
 size_t passA_smem(const DevBasis &b, int rl_smem, int c64);
@@ -203,6 +228,8 @@ struct kry_ham_s {
     int g_dtype, g_m, g_general, g_grid;
     void *g_ws;
     const void *g_G;
+    const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
+    size_t g_ldo, g_ldc;
     cudaStream_t cap_stream;
     void *h_poll;   // pinned host mirror of the control block
     // profiling: CUDA events recorded between the kernels of the captured step
