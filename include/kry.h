@@ -173,6 +173,20 @@ int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, dou
 int kry_profile_enable(kry_ham H, int on);
 int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
 
+/* Launch-shape autotuner (not part of the paper's method).  Times a probe evolution of the
+ * basis state probe_state to t_probe (reps replays after one warm-up, best kept) for each
+ * candidate number of CTAs of the vector kernels: 0 (= the occupancy rule) and 1..4 times
+ * the SM count; keeps the fastest for later calls on H with this dtype and returns it in
+ * *grid_out.  cand_out / ms_out (host, max_cand entries) receive the candidates and their
+ * times, *n_cand how many were tried.  The shape changes only the split of the work and
+ * the order of the per-CTA partial sums. */
+int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_probe, int reps,
+                 int *grid_out, int *cand_out, double *ms_out, int max_cand, int *n_cand,
+                 void *stream);
+/* Set the number of CTAs of the vector kernels for H and dtype (0 = occupancy rule), e.g. a
+ * value cached from an earlier kry_autotune. */
+int kry_set_grid(kry_ham H, int dtype, int grid);
+
 /* Bytes of device workspace kry_evolve allocates for (H, dtype, m); -1 on bad input. */
 int64_t kry_workspace_size(kry_ham H, int dtype, int m);
 

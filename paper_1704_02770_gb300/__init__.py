@@ -50,6 +50,9 @@ SIGNATURES = {
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_workspace_size": (_i64, [_vp, _i, _i]),
+    "kry_autotune": (_i, [_vp, _i, _i, ctypes.c_uint64, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                          _dp, _i, ctypes.POINTER(_i), _vp]),
+    "kry_set_grid": (_i, [_vp, _i, _i]),
     "kry_profile_enable": (_i, [_vp, _i]),
     "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "kry_last_error": (ctypes.c_char_p, []),
@@ -192,6 +195,39 @@ class Hamiltonian:
         _check(load().kry_return_probability(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                              P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
+
+    def autotune(self, state: int, t_probe: float, dtype: str = "c128", m: int = 30, reps: int = 2,
+                 cache: str | None = None, stream=None):
+        """Pick the CTA count of the vector kernels by timing a probe evolution (kry_autotune).
+
+        With `cache` (a JSON file path), a result stored for the same sector, K, dtype, m
+        and GPU is reused instead of measuring, and new results are added to the file."""
+        import json
+        import torch
+        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        key = (f"{torch.cuda.get_device_name()}|L{self.basis.L}|N{self.basis.n_up}|K{self.K}|"
+               f"{dtype}|m{m}")
+        db = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                db = json.load(f)
+            if key in db:
+                _check(load().kry_set_grid(self._h, code, int(db[key]["grid"])))
+                return db[key]
+        g, n = ctypes.c_int(0), ctypes.c_int(0)
+        cand = (ctypes.c_int * 8)()
+        ms = (ctypes.c_double * 8)()
+        _check(load().kry_autotune(self._h, code, m, ctypes.c_uint64(state), float(t_probe), reps,
+                                   ctypes.byref(g), cand, ms, 8, ctypes.byref(n), _stream(stream)))
+        res = {"grid": g.value, "candidates": {int(cand[i]): float(ms[i]) for i in range(n.value)}}
+        if cache:
+            db[key] = res
+            with open(cache, "w") as f:
+                json.dump(db, f, indent=1)
+        return res
+
+    def set_grid(self, grid: int, dtype: str = "c128"):
+        _check(load().kry_set_grid(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, grid))
 
     def grad(self, state: int, t: float, m: int = 30, tol: float = 1e-10, ckpt_every: int = 8,
              stream=None):

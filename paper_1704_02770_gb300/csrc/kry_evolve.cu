@@ -73,7 +73,9 @@ struct EvOpts {
 int grid_for(const kry_ham_s *H, int dtype)
 {
     const DevBasis &b = H->b->dev;
-    return dtype == KRY_C64 ? vector_grid<float2>(b, rl_in_smem(b)) : vector_grid<double2>(b, rl_in_smem(b));
+    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl_in_smem(b)) : vector_grid<double2>(b, rl_in_smem(b));
+    const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
+    return (g > 0 && ov > 0) ? ov : g;   // vector_grid also sets the kernels' smem limits
 }
 
 void drop_graph(kry_ham_s *H)
@@ -339,7 +341,9 @@ int grid_for_b(const kry_ham_s *H, int dtype)
 {
     const DevBasis &b = H->b->dev;
     const int Kp = padded_k(H->K);
-    return dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b)) : batched_grid<double2>(b, Kp, rl_in_smem(b));
+    const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b)) : batched_grid<double2>(b, Kp, rl_in_smem(b));
+    const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
+    return (g > 0 && ov > 0) ? ov : g;
 }
 
 // One Krylov step of the batched path, in groups whose boundaries carry the profile events:

@@ -230,6 +230,7 @@ struct kry_ham_s {
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
     size_t g_ldo, g_ldc;
+    int grid_override[2];       // per precision: CTAs of the vector kernels (0 = occupancy rule)
     cudaStream_t cap_stream;
     void *h_poll;   // pinned host mirror of the control block
     // profiling: CUDA events recorded between the kernels of the captured step
