@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--form", default="c128", choices=["c128", "c64"],
+    ap.add_argument("--form", default="c128", choices=["c128", "c64", "c64b"],
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs): for ncu captures")
@@ -274,6 +274,20 @@ def run_ours(args):
         return e0.elapsed_time(e1) / 1e3, hv, launches, P, st, prof
 
     tune = {}
+    if args.kernels_only and args.form == "c64b":
+        # batched K = 64 ensemble alone (for kernel captures)
+        cb = workloads.config("L22_batched_h1.5")
+        Bb = kry.Basis(cb["L"], cb["n_up"])
+        Hb = kry.Hamiltonian(Bb, cb["J"], cb["Delta"], cb["h"], pbc=cb["pbc"])
+        clk = ClockSampler(local).start()
+        secb, hvb, lb, Pb, stb, profb = timed("c64", 1e-7, profile=True, Hx=Hb, cx=cb)
+        clocks = clk.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": Bb.dim * Hb.K * hvb / secb, "unit": "state-updates/s",
+                              "ms_per_step": 1e3 * secb / args.steps, "workload": "L22_batched_h1.5 K=64 c64",
+                              "roofline": roofline(profb, "c64", Bb.dim * Hb.K, cb, cb["L"], cb["n_up"], clocks),
+                              "clocks": clocks}))
+        return
     form = args.form if args.kernels_only else "c128"
     clk = ClockSampler(local).start()
     sec, hv, launches, P128, st128, prof = timed(form, c["tol"] if form == "c128" else 1e-7,

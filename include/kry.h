@@ -187,6 +187,15 @@ int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_pro
  * value cached from an earlier kry_autotune. */
 int kry_set_grid(kry_ham H, int dtype, int grid);
 
+/* Reorthogonalisation check (a diagnostic; single-realisation evolutions).  Every new
+ * Lanczos vector is orthogonalised against all previous ones by one classical Gram-Schmidt
+ * pass (Sec. 2: Arnoldi orthogonalises each new vector against the whole basis); a second
+ * pass is made only when that pass cancelled most of the vector (||w|| < 0.1 ||H v_j||).
+ * With on = 1 the dots of every new vector with all previous ones are measured after each
+ * pass (kry_stats.max_orth_loss) and subtracted when they exceed 1e-12 ||w|| (complex128) or
+ * 1e-5 ||w|| (complex64). */
+int kry_set_orth_check(kry_ham H, int on);
+
 /* Bytes of device workspace kry_evolve allocates for (H, dtype, m); -1 on bad input. */
 int64_t kry_workspace_size(kry_ham H, int dtype, int m);
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "kry_autotune": (_i, [_vp, _i, _i, ctypes.c_uint64, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                           _dp, _i, ctypes.POINTER(_i), _vp]),
     "kry_set_grid": (_i, [_vp, _i, _i]),
+    "kry_set_orth_check": (_i, [_vp, _i]),
     "kry_profile_enable": (_i, [_vp, _i]),
     "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "kry_last_error": (ctypes.c_char_p, []),
@@ -225,6 +226,10 @@ class Hamiltonian:
             with open(cache, "w") as f:
                 json.dump(db, f, indent=1)
         return res
+
+    def orth_check(self, on: bool = True):
+        """Measure (and subtract when needed) <v_i, w> after every Lanczos update."""
+        _check(load().kry_set_orth_check(self._h, 1 if on else 0))
 
     def set_grid(self, grid: int, dtype: str = "c128"):
         _check(load().kry_set_grid(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, grid))

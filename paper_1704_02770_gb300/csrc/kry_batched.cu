@@ -46,33 +46,43 @@ __device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, co
     V acc[KQ];
 #pragma unroll
     for (int q = 0; q < KQ; ++q) acc[q] = VT<V>::zero();
-    auto gather = [&](uint32_t r2) {
-        const V *xr = x + (size_t)r2 * K;
+    // Neighbour rows in chunks of 4 bond positions (bit 31 = ring bond): the ranks are the
+    // same for all lanes; every lane issues its loads of the whole chunk before summing.
+    const uint32_t hops = anti | (wrap << 31);
 #pragma unroll
-        for (int q = 0; q < KQ; ++q) {
-            const int k = lane + 32 * q;
-            if (k < K) acc[q] = acc[q] + __ldg(xr + k);
+    for (int c0 = 0; c0 < 32; c0 += 4) {
+        if (!((hops >> c0) & 0xFu)) continue;
+        V v[4][KQ];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = c0 + u;
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) v[u][q] = VT<V>::zero();
+            if ((hops >> p) & 1u) {
+                uint32_t t2;
+                if (p == 31) {
+                    const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
+                    t2 = __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask];
+                } else if (p < Llo - 1) {
+                    t2 = base + rl[lo ^ (3u << p)];
+                } else if (p == Llo - 1) {
+                    const uint32_t s2 = s ^ (3u << p);
+                    t2 = __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask];
+                } else {
+                    t2 = __ldg(b.blk + (hi ^ (3u << (p - Llo)))) + off;
+                }
+                const V *xr = x + (size_t)t2 * K;
+#pragma unroll
+                for (int q = 0; q < KQ; ++q) {
+                    const int k = lane + 32 * q;
+                    if (k < K) v[u][q] = __ldg(xr + k);
+                }
+            }
         }
-    };
-    uint32_t a = anti & ((1u << (Llo - 1)) - 1u);
-    while (a) {
-        const int p = __ffs(a) - 1;
-        a &= a - 1u;
-        gather(base + rl[lo ^ (3u << p)]);
-    }
-    if (b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u)) {
-        const uint32_t s2 = s ^ (3u << (Llo - 1));
-        gather(__ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
-    }
-    uint32_t ah = anti >> Llo;
-    while (ah) {
-        const int q = __ffs(ah) - 1;
-        ah &= ah - 1u;
-        gather(__ldg(b.blk + (hi ^ (3u << q))) + off);
-    }
-    if (wrap) {
-        const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
-        gather(__ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) acc[q] = acc[q] + v[u][q];
     }
     const V *xr = x + (size_t)(base + off) * K;
 #pragma unroll

@@ -119,6 +119,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         mark();
         if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, grid, cs);
         mark();
+        if (rc == KRY_OK) rc = launch_dots<V>(a, jj, grid, cs);
         if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, grid, cs);
     }
     mark();
@@ -217,6 +218,8 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     c.n_times = n_times;
     c.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
     c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
+    c.eta_cancel = 0.1;
+    c.verify = H->orth_check;
     if (opt && opt->ckpt) {
         c.ckpt_every = opt->ckpt_every;
         c.ckpt_cap = std::min(opt->ckpt_cap, 64);
@@ -301,7 +304,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (nk + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
+        st->n_launches = launched * (nk + m + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
     }
     if (opt && opt->ckpt) {
         opt->n_ckpt = hp->n_ckpt;

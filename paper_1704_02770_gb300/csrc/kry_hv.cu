@@ -188,14 +188,13 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
     KryCtl *ctl = a.ctl;
     if (ctl->done) return;
     if (MODE <= 1 && jj >= ctl->m_eff) return;
-    if (MODE == 1 && !ctl->corr) return;
+    if (MODE == 1 && !ctl->corr2) return;
     const int nvec = (MODE == 2) ? ctl->m_eff : ((MODE == 3) ? 0 : jj + 1);
     __shared__ V coef[MMAX + 1];
-    __shared__ V wtile[TILE];
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wtmp[NTHR / 32];
     __shared__ int flag;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
     if (tid < nvec) {
         const double2 c = (MODE == 0) ? ctl->coefA[tid] : (MODE == 1) ? ctl->coefC[tid] : ctl->coefY[tid];
@@ -205,7 +204,6 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
     V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
     const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
-    DotAcc<V> acc[4];
     DotAcc<V> nrm, gacc;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t r0 = tile * TILE, r = r0 + tid;
@@ -223,34 +221,6 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
             nrm.add(w, w);
             if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
         }
-        if (MODE == 0) {
-            wtile[tid] = w;
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int iv = warp + 8 * q;
-                if (iv <= jj) {
-                    const V *wi = a.W + (size_t)iv * a.ldW + r0;
-                    V vv[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t rr = lane + 32 * e;
-                        vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
-                    }
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[q].add(vv[e], wtile[lane + 32 * e]);
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (MODE == 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int iv = warp + 8 * q;
-            double2 v = warp_sum(acc[q].value());
-            if (lane == 0 && iv <= jj) red[iv] = v;
-        }
     }
     cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
     if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
@@ -260,21 +230,16 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
     const double nw2 = fin[SLOT_NRM].x;
     const double2 gdot = fin[SLOT_G];
     if (MODE == 0) {
-        double nd2 = 0.0;
-        for (int i = 0; i <= jj; ++i) {
-            const double s = ctl->sigma[i];
-            nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
-        }
-        if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         ctl->vp_kind[1] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
-        if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
+        // One classical Gram-Schmidt pass is enough unless the projection cancelled most of
+        // u (||w|| < eta ||u||, the Daniel-Gragg-Kaufman-Stewart test); then the dots of w
+        // with every previous vector are taken (pass C1) and subtracted if needed (C2).
+        // With orth_check set the dots are taken after every update.
+        if (ctl->verify || nw2 < ctl->eta_cancel * ctl->eta_cancel * ctl->normu2) {
             ctl->corr = 1;
-            for (int i = 0; i <= jj; ++i) {
-                const double s = ctl->sigma[i];
-                ctl->coefC[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
-            }
-            ctl->alpha[jj] += fin[jj].x * ctl->sigma[jj];
+            ctl->wnorm2 = nw2;
+            ctl->wg = gdot;
         } else {
             ctl->corr = 0;
             finalize_beta(ctl, jj, nw2, gdot);
@@ -283,7 +248,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
         ctl->n_corr += 1;
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         ctl->vp_kind[2] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
-        ctl->corr = 0;
+        ctl->corr2 = 0;
         finalize_beta(ctl, jj, nw2, gdot);
     } else {
         const double b0 = sqrt(nw2);
@@ -300,7 +265,79 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
         if (MODE == 2) ctl->vp_kind[4] += (double)(nvec + 1) + (a.G ? 1.0 : 0.0);
         ctl->m_eff = ctl->m;
         ctl->corr = 0;
+        ctl->corr2 = 0;
         if (MODE == 2 && ctl->finishing) ctl->done = 1;
+    }
+    ctl->counter = 0;
+}
+
+// Pass C1: dots <v_i, w> of the new vector w = W_{j+1} with every earlier vector, when pass B
+// flagged them (severe cancellation, or orth_check).  Subtracts them in pass C2 when they
+// exceed eta_corr ||w||; otherwise w is accepted as it is.
+template <class V>
+__global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done || jj >= ctl->m_eff || !ctl->corr) return;
+    __shared__ V wtile[TILE];
+    __shared__ double2 red[PSTRIDE];
+    __shared__ int flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    const V *w = a.W + (size_t)(jj + 1) * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    DotAcc<V> acc[4];
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TILE;
+        __syncthreads();
+        wtile[tid] = (r0 + tid < D) ? __ldg(w + r0 + tid) : VT<V>::zero();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iv = warp + 8 * q;
+            if (iv <= jj) {
+                const V *wi = a.W + (size_t)iv * a.ldW + r0;
+                V vv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t rr = lane + 32 * e;
+                    vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[q].add(vv[e], wtile[lane + 32 * e]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int iv = warp + 8 * q;
+        double2 v = warp_sum(acc[q].value());
+        if (lane == 0 && iv <= jj) red[iv] = v;
+    }
+    __syncthreads();
+    double2 *fin = red;
+    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (tid != 0) return;
+    const double nw2 = ctl->wnorm2;
+    double nd2 = 0.0;
+    for (int i = 0; i <= jj; ++i) {
+        const double s = ctl->sigma[i];
+        nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
+    }
+    if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
+    ctl->vec_passes += (double)(jj + 2);
+    ctl->vp_kind[2] += (double)(jj + 2);
+    ctl->corr = 0;
+    if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
+        ctl->corr2 = 1;
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i];
+            ctl->coefC[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
+        }
+        ctl->alpha[jj] += fin[jj].x * ctl->sigma[jj];
+    } else {
+        ctl->corr2 = 0;
+        finalize_beta(ctl, jj, nw2, ctl->wg);
     }
     ctl->counter = 0;
 }
@@ -549,6 +586,16 @@ template int launch_vecout<double2>(const VecOutArgs<double2> &, int, cudaStream
 template int launch_vecout<float2>(const VecOutArgs<float2> &, int, cudaStream_t);
 template int launch_ckpt<double2>(const double2 *, double2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
+template <class V>
+int launch_dots(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+{
+    k_dots<V><<<grid, NTHR, 0, s>>>(a, jj);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+template int launch_dots<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
+template int launch_dots<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
 template int vector_grid<double2>(const DevBasis &, int);
 template int vector_grid<float2>(const DevBasis &, int);
 template int launch_passA<double2>(const EvArgs<double2> &, int, int, cudaStream_t);

@@ -136,6 +136,10 @@ struct KryCtl {
     int m, m_eff, corr, finishing, done, err;
     int n_times, next_out, r0;
     unsigned int counter;      // ticket of the last-CTA reductions
+    // second Gram-Schmidt pass: corr = take the dots of w (pass C1), corr2 = subtract them (C2)
+    int corr2, verify;
+    double eta_cancel, wnorm2;
+    double2 wg;
     // dense vector output (outputs [out_begin, out_end) of the current step) and checkpoints
     int out_begin, out_end;
     int ckpt_every, n_ckpt, ckpt_cap;
@@ -195,6 +199,7 @@ int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, voi
 template <class V> int launch_passA(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
 template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid,
                                       cudaStream_t s);
+template <class V> int launch_dots(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
 template <class V> int vector_grid(const DevBasis &b, int rl_smem);
 int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
 // small exponential (kry_exp.cu)
@@ -231,6 +236,7 @@ struct kry_ham_s {
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
     size_t g_ldo, g_ldc;
     int grid_override[2];       // per precision: CTAs of the vector kernels (0 = occupancy rule)
+    int orth_check;             // measure <v_i, w> after every Lanczos update
     cudaStream_t cap_stream;
     void *h_poll;   // pinned host mirror of the control block
     // profiling: CUDA events recorded between the kernels of the captured step

@@ -11,6 +11,13 @@
 
 using namespace kry;
 
+extern "C" int kry_set_orth_check(kry_ham H, int on)
+{
+    if (!H) { set_error("kry_set_orth_check: H is NULL"); return KRY_EINVAL; }
+    H->orth_check = on ? 1 : 0;
+    return KRY_OK;
+}
+
 extern "C" int kry_set_grid(kry_ham H, int dtype, int grid)
 {
     if (!H || grid < 0 || (dtype != KRY_C128 && dtype != KRY_C64)) {
