@@ -29,6 +29,7 @@ def nvcc() -> str:
 
 def flags(ptxas_verbose: bool = False) -> list[str]:
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                "--Werror", "cross-execution-space-call",
                 "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
     if ptxas_verbose:
         f += ["-Xptxas", "-v"]

@@ -158,13 +158,25 @@ extern "C" int kry_basis_create(int L, int n_up, kry_basis *out)
         if (blk[hi] == INV) blk[hi] = next;
         else next = blk[hi];
     }
+    // block of the first rank of every tile: the largest hi with blk[hi] <= t * TILE
+    const uint64_t ntiles = (D + TILE - 1) / TILE;
+    std::vector<uint32_t> tstart(ntiles > 0 ? ntiles : 1, 0);
+    {
+        uint32_t hi = 0;
+        for (uint64_t t = 0; t < ntiles; ++t) {
+            const uint64_t r = t * TILE;
+            while (hi + 1 < nhi && blk[hi + 1] <= r) ++hi;
+            tstart[t] = hi;
+        }
+    }
     // device upload: one allocation holding every table and the error flag
     size_t o_blk = 0, o_rl = o_blk + sizeof(uint32_t) * nhi;
     size_t o_ll = o_rl + sizeof(uint16_t) * nlo;
     size_t o_ko = (o_ll + sizeof(uint16_t) * nlo + 15) & ~(size_t)15;
     size_t o_bs = o_ko + sizeof(uint32_t) * (Llo + 2);
     size_t o_er = (o_bs + sizeof(uint32_t) * (Llo + 1) + 15) & ~(size_t)15;
-    size_t bytes = o_er + 16;
+    size_t o_ts = o_er + 16;
+    size_t bytes = o_ts + sizeof(uint32_t) * tstart.size();
     kry_basis b = new (std::nothrow) kry_basis_s();
     if (!b) { set_error("kry_basis_create: host allocation failed"); return KRY_ENOMEM; }
     b->L = L; b->N = n_up; b->Llo = Llo; b->Lhi = Lhi; b->D = (int64_t)D;
@@ -177,10 +189,12 @@ extern "C" int kry_basis_create(int L, int n_up, kry_basis *out)
     cudaMemcpy(base + o_ll, lolist.data(), sizeof(uint16_t) * nlo, cudaMemcpyHostToDevice);
     cudaMemcpy(base + o_ko, koff.data(), sizeof(uint32_t) * (Llo + 2), cudaMemcpyHostToDevice);
     cudaMemcpy(base + o_bs, bsz.data(), sizeof(uint32_t) * (Llo + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(base + o_ts, tstart.data(), sizeof(uint32_t) * tstart.size(), cudaMemcpyHostToDevice);
     e = cudaMemset(base + o_er, 0, 16);
     if (e != cudaSuccess) { cudaFree(b->d_tab); delete b; return cuda_fail(e, "table upload"); }
     DevBasis &d = b->dev;
     d.blk = (const uint32_t *)(base + o_blk);
+    d.tstart = (const uint32_t *)(base + o_ts);
     d.ranklo = (const uint16_t *)(base + o_rl);
     d.lolist = (const uint16_t *)(base + o_ll);
     d.koff = (const uint32_t *)(base + o_ko);

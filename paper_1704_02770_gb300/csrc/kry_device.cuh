@@ -92,9 +92,58 @@ struct DotAccF {
         return make_double2((double)sr + (double)cr, (double)si + (double)ci);
     }
 };
+// complex64 dots with packed FP32x2 arithmetic (sm_100 and later): the same error-free
+// products and TwoSum as DotAccF, two components per instruction.  With b_x2 = (bx, bx)
+// and b_y2 = (by, by), the pair products a*b_x2 = (ax bx, ay bx) and a*b_y2 = (ax by, ay by)
+// are summed into two float-float pairs; conj(a) b = (ax bx + ay by, ax by - ay bx) is formed
+// in FP64 at the end.
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void ff_pair_add(float2 &s, float2 &c, float2 a, float2 b)
+{
+    const float2 p = __fmul2_rn(a, b);
+    const float2 e = __ffma2_rn(a, b, make_float2(-p.x, -p.y));   // a*b - p, exact
+    const float2 t = __fadd2_rn(s, p);
+    const float2 z = fsub2(t, s);
+    const float2 err = __fadd2_rn(fsub2(s, fsub2(t, z)), fsub2(p, z));
+    s = t;
+    c = __fadd2_rn(c, __fadd2_rn(err, e));
+}
+struct DotAccF2 {
+    float2 s1 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+    float2 s2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+    // b4 = (bx, bx, by, by)
+    __device__ __forceinline__ void add(float2 a, float4 b4)
+    {
+        ff_pair_add(s1, c1, a, make_float2(b4.x, b4.y));
+        ff_pair_add(s2, c2, a, make_float2(b4.z, b4.w));
+    }
+    __device__ __forceinline__ double2 value() const
+    {
+        const double axbx = (double)s1.x + (double)c1.x, aybx = (double)s1.y + (double)c1.y;
+        const double axby = (double)s2.x + (double)c2.x, ayby = (double)s2.y + (double)c2.y;
+        return make_double2(axbx + ayby, axby - aybx);
+    }
+};
+
 template <class V> struct DotAcc;
 template <> struct DotAcc<double2> : DotAccD {};
 template <> struct DotAcc<float2> : DotAccF {};
+
+// Streaming dots against a fixed tile y (the right operand, staged in shared memory once
+// per tile): complex64 keeps y expanded as (yx, yx, yy, yy) for the packed accumulator.
+template <class V> struct TileDot;
+template <> struct TileDot<double2> {
+    using Acc = DotAccD;
+    using Y = double2;
+    __device__ __forceinline__ static Y expand(double2 u) { return u; }
+    __device__ __forceinline__ static Y zero() { return make_double2(0.0, 0.0); }
+};
+template <> struct TileDot<float2> {
+    using Acc = DotAccF2;
+    using Y = float4;
+    __device__ __forceinline__ static Y expand(float2 u) { return make_float4(u.x, u.x, u.y, u.y); }
+    __device__ __forceinline__ static Y zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
 
 __device__ __forceinline__ double2 warp_sum(double2 v)
 {
@@ -108,23 +157,13 @@ __device__ __forceinline__ double2 warp_sum(double2 v)
 
 // ---------------------------------------------------------------- rank tables
 
-__device__ __forceinline__ uint32_t find_block(const DevBasis &b, uint32_t r)
-{
-    uint32_t lo = 0, cnt = 1u << b.Lhi;
-    while (cnt > 0) {
-        uint32_t step = cnt >> 1;
-        if (__ldg(b.blk + lo + step) <= r) { lo += step + 1; cnt -= step + 1; }
-        else cnt = step;
-    }
-    return lo - 1;
-}
-
-// Locate rank r0 + t (< D) as (block hi, offset in block, particles in the lower part).
+// Locate rank r0 + t (< D) as (block hi, offset in block, particles in the lower part):
+// start from the block of the enclosing tile's first rank and step over whole blocks.
 __device__ __forceinline__ void tile_unrank(const DevBasis &b, const uint32_t *bsz_s, uint32_t r0,
                                             uint32_t t, uint32_t &hi, uint32_t &off, int &klo)
 {
     const uint32_t nhi = 1u << b.Lhi;
-    uint32_t h = find_block(b, r0);
+    uint32_t h = __ldg(b.tstart + r0 / (uint32_t)TILE);
     uint32_t o = r0 - __ldg(b.blk + h) + t;
     int k = b.N - __popc(h);
     while (o >= bsz_s[k]) {
@@ -195,6 +234,77 @@ __device__ __forceinline__ V hv_row(const DevBasis &b, const DevHam &hm, const V
         acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
     return axpby(d, __ldg(x + base + off), (R)hm.halfJ, acc);
+}
+
+// The same row with the hop amplitudes requested in batches of HB: the targets of a batch
+// are formed first, then its loads are issued together, then summed (an unused slot adds
+// zero, so this suits complex64, where adds are cheap).  Bonds inside the lower part keep
+// the block (target base + ranklo[lo']); bonds inside the upper part keep the offset
+// (target blk[hi'] + off, blk staged in shared memory when blk_s is set); the bond joining
+// the halves and the ring bond take both lookups.
+template <class V, int HB>
+__device__ __forceinline__ V hv_row_batched(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
+                                            uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
+                                            const uint16_t *rl, const uint32_t *blk_s)
+{
+    using R = typename VT<V>::R;
+    const int Llo = b.Llo, L = b.L;
+    const uint32_t pos = koff_s[klo] + off;
+    const uint32_t lo = __ldg(b.lolist + pos);
+    const uint32_t s = (hi << Llo) | lo;
+    const uint32_t base = blk_s ? blk_s[hi] : __ldg(b.blk + hi);
+    const uint32_t lomask = (1u << Llo) - 1u;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint32_t anti = (s ^ (s >> 1)) & obc;
+    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
+    const int nanti = __popc(anti) + (int)wrap;
+    const R d = (R)hm.cz * (R)(hm.nbonds - 2 * nanti) + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
+    const V xd = __ldg(x + base + off);
+    V acc = VT<V>::zero();
+    auto blkv = [&](uint32_t h) { return blk_s ? blk_s[h] : __ldg(b.blk + h); };
+    // the masks keep every table index in range even for an unused slot
+    const uint32_t himask = (1u << b.Lhi) - 1u;
+    // bonds inside the lower part
+    uint32_t al = anti & ((1u << (Llo - 1)) - 1u);
+    while (al) {
+        uint32_t idx[HB];
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            const int p = __ffs(al) - 1;
+            al &= al - 1u;
+            idx[c] = p < 0 ? 0xffffffffu : base + rl[(lo ^ (3u << (p & 31))) & lomask];
+        }
+        V v[HB];
+#pragma unroll
+        for (int c = 0; c < HB; ++c) v[c] = idx[c] != 0xffffffffu ? __ldg(x + idx[c]) : VT<V>::zero();
+#pragma unroll
+        for (int c = 0; c < HB; ++c) acc = acc + v[c];
+    }
+    // bonds inside the upper part
+    uint32_t ah = anti >> Llo;
+    while (ah) {
+        uint32_t idx[HB];
+#pragma unroll
+        for (int c = 0; c < HB; ++c) {
+            const int q = __ffs(ah) - 1;
+            ah &= ah - 1u;
+            idx[c] = q < 0 ? 0xffffffffu : blkv((hi ^ (3u << (q & 31))) & himask) + off;
+        }
+        V v[HB];
+#pragma unroll
+        for (int c = 0; c < HB; ++c) v[c] = idx[c] != 0xffffffffu ? __ldg(x + idx[c]) : VT<V>::zero();
+#pragma unroll
+        for (int c = 0; c < HB; ++c) acc = acc + v[c];
+    }
+    // the bond joining the halves, and the ring bond (L-1, 0)
+    const bool jn = b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u);
+    const uint32_t sj = s ^ (3u << (Llo - 1)), sr = s ^ ((1u << (L - 1)) | 1u);
+    const uint32_t ij = jn ? blkv((sj >> Llo) & himask) + rl[sj & lomask] : 0u;
+    const uint32_t ir = wrap ? blkv((sr >> Llo) & himask) + rl[sr & lomask] : 0u;
+    const V vj = jn ? __ldg(x + ij) : VT<V>::zero();
+    const V vr = wrap ? __ldg(x + ir) : VT<V>::zero();
+    acc = acc + vj + vr;
+    return axpby(d, xd, (R)hm.halfJ, acc);
 }
 
 }  // namespace kry

@@ -3,8 +3,8 @@
 // kry_apply / kry_evolve / kry_return_probability.
 //
 // One Krylov step, captured once per (precision, m) and replayed:
-//   for j = 0..m-1:  pass A (u = H v_j + dots)  ->  pass B (update + second-pass dots)
-//                    ->  pass C (correction, runs only when flagged)
+//   for j = 0..m-1:  pass A (u = H v_j, then the dots <v_i, u>)  ->  pass B (update)
+//                    ->  pass C (second Gram-Schmidt pass, runs only when flagged)
 //   small exponential + step control + dense output of P  ->  combine psi = beta V y.
 // Device flags end the Lanczos loop early on an invariant subspace and turn every kernel
 // into a no-op once the last output time is reached; the host only polls that flag.
@@ -70,11 +70,16 @@ struct EvOpts {
     double ckpt_t[64] = {};    // out
 };
 
-int grid_for(const kry_ham_s *H, int dtype)
+// CTAs of the streaming dots (returned), of the H.v (*gridH) and of the updates (*gridB);
+// an autotuned override sets the two streaming grids.
+int grid_for(const kry_ham_s *H, int dtype, int *gridH, int *gridB)
 {
     const DevBasis &b = H->b->dev;
-    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl_in_smem(b)) : vector_grid<double2>(b, rl_in_smem(b));
+    const int rl = rl_in_smem(b);
+    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl, gridH, gridB)
+                                   : vector_grid<double2>(b, rl, gridH, gridB);
     const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
+    if (g > 0 && ov > 0) *gridB = ov;
     return (g > 0 && ov > 0) ? ov : g;   // vector_grid also sets the kernels' smem limits
 }
 
@@ -94,8 +99,8 @@ int kind_of(int k, int m)
 }
 
 template <class V>
-int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int grid,
-                 const EvOpts *opt)
+int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int grid, int gridH,
+                 int gridB, const EvOpts *opt)
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
@@ -115,12 +120,13 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     };
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
         mark();
-        rc = launch_passA<V>(a, jj, grid, cs);
+        rc = launch_hv<V>(a, jj, gridH, cs);
+        if (rc == KRY_OK) rc = launch_dots<V>(a, 0, jj, grid, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, gridB, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_dots<V>(a, jj, grid, cs);
-        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_dots<V>(a, 1, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, gridB, cs);
     }
     mark();
     if (rc == KRY_OK) rc = launch_smallexp(ea, cs);
@@ -133,12 +139,12 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         va.ldOut = opt->ldOut;
         va.ctl = a.ctl;
         va.D = a.b.D;
-        rc = launch_vecout<V>(va, grid, cs);
+        rc = launch_vecout<V>(va, gridB, cs);
     }
     mark();
-    if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, grid, cs);
+    if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, gridB, cs);
     if (rc == KRY_OK && opt && opt->ckpt)
-        rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, grid, cs);
+        rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, gridB, cs);
     mark();
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -155,9 +161,10 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
              kry_stats *st, cudaStream_t s, EvOpts *opt = nullptr)
 {
     const DevBasis &b = H->b->dev;
-    const int grid = grid_for(H, dtype);
+    int gridH = 0, gridB = 0;
+    const int grid = grid_for(H, dtype, &gridH, &gridB);
     if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
-    const Layout l = layout(H, dtype, m, grid, n_times);
+    const Layout l = layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), n_times);
     if (!H->ws || H->ws_bytes < l.bytes) {
         drop_graph(H);
         if (H->ws) cudaFree(H->ws);
@@ -191,14 +198,16 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     const void *vkey = opt ? opt->vec_out : nullptr, *ckey = opt ? opt->ckpt : nullptr;
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
-                     H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
+                     H->g_grid != grid || H->g_gridB != gridB || H->g_gridH != gridH || H->g_ws != H->ws ||
+                     H->g_G != (const void *)(base + l.oP) ||
                      H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
                      H->g_vec != vkey || H->g_ck != ckey ||
                      (opt && (H->g_ldo != opt->ldOut || H->g_ldc != opt->ldC))))
         drop_graph(H);
     if (!H->gexec) {
-        if (int rc = capture_step<V>(H, a, ea, m, grid, opt)) return rc;
-        H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid;
+        if (int rc = capture_step<V>(H, a, ea, m, grid, gridH, gridB, opt)) return rc;
+        H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid; H->g_gridB = gridB;
+        H->g_gridH = gridH;
         H->g_ws = H->ws; H->g_G = base + l.oP;
         H->g_vec = vkey; H->g_ck = ckey;
         H->g_ldo = opt ? opt->ldOut : 0;
@@ -241,7 +250,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
     if (general) {
         KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
-        if (int rc = launch_lincomb<V>(a, 3, 0, grid, s)) return rc;
+        if (int rc = launch_lincomb<V>(a, 3, 0, gridB, s)) return rc;
     } else {
         KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
         if (int rc = launch_set_basis_state(a.W, dtype == KRY_C64, (uint32_t)c.r0, s)) return rc;
@@ -267,7 +276,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
                 H->prof_launches[kind_of(k, m)] += 1;
             }
         }
-        if (hp->done) break;
+        if (hp->done || hp->err) break;
         if (launched >= max_launch) {
             set_error("kry_evolve: no convergence after %lld Krylov steps (t = %g of %g)", launched,
                       hp->t_now, hp->t_end);
@@ -285,6 +294,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
         if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
+        else if (hp->err == KRY_ECUDA) set_error("kry_evolve: a tile copy did not complete within its wait limit");
         else set_error("kry_evolve: initial vector has zero norm");
         return hp->err;
     }
@@ -304,7 +314,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (nk + m + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
+        st->n_launches = launched * (nk + 2 * m + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
     }
     if (opt && opt->ckpt) {
         opt->n_ckpt = hp->n_ckpt;
@@ -516,7 +526,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
                 H->prof_launches[kind_of(k, m)] += 1;
             }
         }
-        if (hp->done) break;
+        if (hp->done || hp->err) break;
         if (launched >= max_launch) {
             set_error("kry_evolve: no convergence after %lld Krylov steps (t = %g of %g)", launched,
                       hp->t_now, hp->t_end);
@@ -608,9 +618,10 @@ extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *l
 extern "C" int64_t kry_workspace_size(kry_ham H, int dtype, int m)
 {
     if (!H || m < 1 || m > MMAX || (dtype != KRY_C128 && dtype != KRY_C64)) return -1;
-    const int grid = grid_for(H, dtype);
+    int gridH = 0, gridB = 0;
+    const int grid = grid_for(H, dtype, &gridH, &gridB);
     if (grid <= 0) return -1;
-    return (int64_t)layout(H, dtype, m, grid, 1).bytes;
+    return (int64_t)layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), 1).bytes;
 }
 
 extern "C" int kry_apply(kry_ham H, int dtype, const void *d_x, void *d_y, void *stream)

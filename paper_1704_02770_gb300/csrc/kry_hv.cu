@@ -1,7 +1,8 @@
 // Vector kernels of the Krylov step (Sec. 2, "Krylov subspace methods"):
 //   k_apply     y = H x (matrix-free, Eq. 1)
-//   k_passA     u = H v_j fused with all dots <v_i, u>, i <= j (alpha_j and the first
-//               reorthogonalisation pass share one sweep over HBM)
+//   k_hv        u = sigma_j H v_j with alpha_j = <v_j, u> and ||u||^2 (pass A, part 1)
+//   k_dots      <v_i, y> for the earlier vectors, streamed through shared memory by the
+//               bulk-copy engine (pass A part 2 with y = u; pass C1 with y = w)
 //   k_lincomb   w = src - sum_i c_i W_i with an optional second sweep of dots
 //               (MODE 0: Lanczos update + second-pass dots; 1: second-pass correction;
 //                2: combine psi = beta V y; 3: load the initial vector)
@@ -12,6 +13,7 @@
 #include <algorithm>
 
 #include "kry_device.cuh"
+#include "kry_stream.cuh"
 
 namespace kry {
 
@@ -46,11 +48,17 @@ __global__ void __launch_bounds__(NTHR) k_apply(DevBasis b, DevHam hm, const V *
 
 // ---------------------------------------------------------------- reductions
 
-// Write this CTA's partials, then let the last CTA sum all partials (CTA order) into
-// fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).
+// Write this CTA's partials, then let the last CTA to finish sum all partials into
+// fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).  The sum is spread over
+// FGROUPS x PSTRIDE threads: thread (g, slot) adds the partials of CTAs g, g+FGROUPS, ...
+// (neighbouring threads read neighbouring slots, so the loads coalesce and none waits on
+// another), then the FGROUPS group sums are added in group order.  The summation order
+// depends only on the grid, so results are bitwise reproducible for a fixed grid.
+constexpr int FGROUPS = NTHR / PSTRIDE;   // 6
 __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *part, KryCtl *ctl,
                                                 double2 *fin, int *flag, unsigned *counter = nullptr)
 {
+    __shared__ double2 gsum[FGROUPS][PSTRIDE];
     const int tid = threadIdx.x;
     if (!counter) counter = &ctl->counter;
     if (tid < PSTRIDE) part[(size_t)blockIdx.x * PSTRIDE + tid] = red[tid];
@@ -60,12 +68,23 @@ __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *par
     __syncthreads();
     if (!*flag) return false;
     __threadfence();
-    if (tid < PSTRIDE) {
+    if (tid < FGROUPS * PSTRIDE) {
+        const int g = tid / PSTRIDE, slot = tid - g * PSTRIDE;
         double2 s = make_double2(0.0, 0.0);
-        for (unsigned c = 0; c < gridDim.x; ++c) {
-            double2 v = __ldcg(part + (size_t)c * PSTRIDE + tid);
+#pragma unroll 8
+        for (unsigned c = g; c < gridDim.x; c += FGROUPS) {
+            const double2 v = __ldcg(part + (size_t)c * PSTRIDE + slot);
             s.x += v.x;
             s.y += v.y;
+        }
+        gsum[g][slot] = s;
+    }
+    __syncthreads();
+    if (tid < PSTRIDE) {
+        double2 s = gsum[0][tid];
+        for (int g = 1; g < FGROUPS; ++g) {
+            s.x += gsum[g][tid].x;
+            s.y += gsum[g][tid].y;
         }
         fin[tid] = s;
     }
@@ -88,86 +107,7 @@ __device__ __forceinline__ void cta_sum_into(double2 v, double2 *red, int slot, 
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- pass A
-
-template <class V>
-__global__ void __launch_bounds__(NTHR, 2) k_passA(EvArgs<V> a, int jj)
-{
-    KryCtl *ctl = a.ctl;
-    if (ctl->done || jj >= ctl->m_eff) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    V *utile = (V *)smem;
-    double2 *red = (double2 *)(smem + sizeof(V) * TILE);
-    double2 *wtmp = red + PSTRIDE;
-    SmemHead *hd = (SmemHead *)(wtmp + NTHR / 32);
-    int *flag = (int *)(hd + 1);
-    uint16_t *rl_s = (uint16_t *)(flag + 4);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
-    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
-    __syncthreads();
-    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
-    const double sj = ctl->sigma[jj];
-    const V *x = a.W + (size_t)jj * a.ldW;
-    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
-    DotAcc<V> acc[4];
-    DotAcc<V> nrm;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * TILE;
-        V u = VT<V>::zero();
-        if (r0 + tid < D) {
-            uint32_t hi, off;
-            int klo;
-            tile_unrank(a.b, hd->bsz, r0, tid, hi, off, klo);
-            u = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
-            a.U[r0 + tid] = u;
-            nrm.add(u, u);
-        }
-        utile[tid] = u;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int iv = warp + 8 * q;
-            if (iv <= jj) {
-                const V *wi = a.W + (size_t)iv * a.ldW + r0;
-                V vv[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t rr = lane + 32 * e;
-                    vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) acc[q].add(vv[e], utile[lane + 32 * e]);
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int iv = warp + 8 * q;
-        double2 v = warp_sum(acc[q].value());
-        if (lane == 0 && iv <= jj) red[iv] = v;
-    }
-    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
-    double2 *fin = red;   // reused after the partials are written
-    if (!finish_partials(red, a.part, ctl, fin, flag)) return;
-    if (tid == 0) {
-        for (int i = 0; i <= jj; ++i) {
-            const double s = ctl->sigma[i];
-            const double2 c = make_double2(fin[i].x * s, fin[i].y * s);   // <v_i, u>
-            ctl->coefA[i] = make_double2(c.x * s, c.y * s);
-            if (i == jj) ctl->alpha[jj] = c.x;
-        }
-        ctl->normu2 = fin[SLOT_NRM].x;
-        ctl->n_hv += 1;
-        ctl->vec_passes += (double)(jj + 2);
-        ctl->vp_kind[0] += (double)(jj + 2);
-        ctl->counter = 0;
-    }
-}
-
-// ---------------------------------------------------------------- linear combinations
-
+// beta_j = ||w|| and the scale of the next vector, or the end of the Krylov space
 __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, double2 gdot)
 {
     const double bt = sqrt(nw2);
@@ -182,8 +122,231 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
     }
 }
 
+// ---------------------------------------------------------------- tile streaming
+
+// k_dots: NCW consumer warps and one producer warp
+constexpr int NCW = 8;
+constexpr int NTHR_WS = (NCW + 1) * 32;
+static_assert(NCW == GV, "one consumer warp per chunk of a unit");
+
+// ---------------------------------------------------------------- pass A
+
+// u = sigma_j H W_j, written to U, with <W_j, u> (alpha_j) and ||u||^2 reduced on the way
+// (W_j[r] is read for the diagonal term anyway).  One thread per row at full occupancy:
+// the gathers of the hops are latency-bound, so as many rows as possible are kept in
+// flight; the dots with the earlier vectors are a separate stream (k_dots, mode 0).
+template <class V>
+__global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done || jj >= ctl->m_eff) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemHead *hd = (SmemHead *)smem;
+    uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHead));
+    __shared__ double2 red[PSTRIDE];
+    __shared__ double2 wtmp[NTHR / 32];
+    __shared__ int flag;
+    const int tid = threadIdx.x;
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
+    __syncthreads();
+    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
+    const double sj = ctl->sigma[jj];
+    const V *x = a.W + (size_t)jj * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    DotAcc<V> nrm, dxu;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TILE, r = r0 + tid;
+        if (r < D) {
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(a.b, hd->bsz, r0, tid, hi, off, klo);
+            const V u = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
+            a.U[r] = u;
+            nrm.add(u, u);
+            dxu.add(__ldg(x + r), u);
+        }
+    }
+    cta_sum_into(dxu.value(), red, 0, wtmp);
+    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
+    double2 *fin = red;
+    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (tid == 0) {
+        const double s = ctl->sigma[jj];
+        const double2 c = make_double2(fin[0].x * s, fin[0].y * s);   // <v_j, u>
+        ctl->coefA[jj] = make_double2(c.x * s, c.y * s);
+        ctl->alpha[jj] = c.x;
+        ctl->normu2 = fin[SLOT_NRM].x;
+        ctl->n_hv += 1;
+        ctl->vec_passes += 2.0;
+        ctl->vp_kind[0] += 2.0;
+        ctl->counter = 0;
+    }
+}
+
+// Dots <W_i, y> of a right-hand vector y with the earlier Krylov vectors, streamed through
+// the ring by a producer warp (warp NCW, one lane issuing the bulk copies) to NCW consumer
+// warps.  Unit 0 of a tile carries y's rows (each consumer lane keeps its eight rows in
+// registers), units 1.. carry up to GV vectors W_i, one per consumer warp.  A consumer warp
+// hands a slot back with one arrival on the slot's "empty" barrier; no CTA-wide barrier
+// is taken per unit, so the warps run ahead of one another.
+//   MODE 0 (pass A, j >= 1): y = U = sigma_j H W_j, i < j; fills coefA[0..j).
+//   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}, i <= j; measures the loss of
+//          orthogonality and sets up the subtraction of pass C2 when it exceeds eta_corr.
 template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
+__global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr)
+{
+    KryCtl *ctl = a.ctl;
+    if (ctl->done || jj >= ctl->m_eff) return;
+    if (MODE == 0 && jj == 0) return;
+    if (MODE == 1 && !ctl->corr) return;
+    using Y = typename TileDot<V>::Y;
+    __shared__ double2 red[PSTRIDE];
+    __shared__ int flag;
+    __shared__ volatile int abort_s;
+    __shared__ uint32_t issued_s;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *empty = (uint64_t *)(smem + 64);
+    const Ring R{(uint64_t *)smem, smem + 128, nr, (uint32_t)(TILE * sizeof(V))};
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
+    if (tid == 0) {
+        for (int i = 0; i < nr; ++i) {
+            mbar_init(R.bar + i, 1);
+            mbar_init(empty + i, NCW);
+        }
+        fence_barrier_init();
+        abort_s = 0;
+        issued_s = 0;
+    }
+    __syncthreads();
+    const V *y = (MODE == 0) ? a.U : a.W + (size_t)(jj + 1) * a.ldW;
+    const int nv = (MODE == 0) ? jj : jj + 1;   // vectors W_0 .. W_{nv-1}
+    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    const int nch = 1 + nv, ng = 1 + (nv + GV - 1) / GV;
+    const uint32_t nq = cta_tiles(ntiles) * (uint32_t)ng;
+    if (warp == NCW) {
+        // producer: refill slot q % nr once all consumer warps have released it
+        if (lane == 0) {
+            const V *W = a.W;
+            const size_t ldW = a.ldW;
+            auto ptr = [W, ldW, y](int c) { return c == 0 ? y : W + (size_t)(c - 1) * ldW; };
+            uint32_t q = 0;
+            for (; q < nq; ++q) {
+                const int st = (int)(q % (uint32_t)nr);
+                if (q >= (uint32_t)nr && !mbar_wait(empty + st, ((q / (uint32_t)nr) - 1u) & 1u)) abort_s = 1;
+                if (abort_s) break;
+                ring_issue<V>(R, q, ng, nch, 1, D, ptr);
+            }
+            issued_s = q;
+        }
+    } else {
+        typename TileDot<V>::Acc acc[MMAX / GV];
+        uint32_t q = 0;
+        for (uint32_t tile = blockIdx.x; tile < ntiles && !abort_s; tile += gridDim.x) {
+            const uint32_t r0 = tile * TILE;
+            const bool full_tile = r0 + TILE <= D;
+            Y yv[8];
+            {   // unit 0: this lane's rows of y
+                const int st = (int)(q % (uint32_t)nr);
+                if (!mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u)) { abort_s = 1; break; }
+                const V *ys = (const V *)R.slot(st, 0);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t rr = lane + 32 * e;
+                    yv[e] = (full_tile || r0 + rr < D) ? TileDot<V>::expand(ys[rr]) : TileDot<V>::zero();
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + st);
+                ++q;
+            }
+            bool ok = true;
+#pragma unroll
+            for (int g = 0; g < MMAX / GV; ++g) {
+                if (g + 1 < ng && ok) {
+                    const int st = (int)(q % (uint32_t)nr);
+                    ok = mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u);
+                    if (ok && g * GV + warp < nv) {
+                        const V *wi = (const V *)R.slot(st, warp);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t rr = lane + 32 * e;
+                            // slot rows past D hold stale data
+                            const V wv = (full_tile || r0 + rr < D) ? wi[rr] : VT<V>::zero();
+                            acc[g].add(wv, yv[e]);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + st);
+                    ++q;
+                }
+            }
+            if (!ok) { abort_s = 1; break; }
+        }
+#pragma unroll
+        for (int g = 0; g < MMAX / GV; ++g) {
+            const int iv = g * GV + warp;
+            double2 v = warp_sum(acc[g].value());
+            if (lane == 0 && iv < nv) red[iv] = v;
+        }
+    }
+    __syncthreads();
+    if (abort_s) {   // a wait timed out: let the copies in flight land, then give up
+        if (tid == 0) {
+            const uint32_t n = issued_s;
+            for (uint32_t p = n > (uint32_t)nr ? n - (uint32_t)nr : 0u; p < n; ++p)
+                mbar_wait(R.bar + p % (uint32_t)nr, (p / (uint32_t)nr) & 1u);
+            // only the error is recorded: the host stops on it, while every kernel still
+            // running reads a consistent done flag
+            ctl->err = KRY_ECUDA;
+            __threadfence();
+        }
+        return;
+    }
+    double2 *fin = red;
+    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (tid != 0) return;
+    if (MODE == 0) {
+        for (int i = 0; i < jj; ++i) {
+            const double s = ctl->sigma[i];
+            ctl->coefA[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);   // <v_i, u> sigma_i
+        }
+        ctl->vec_passes += (double)(jj + 1);
+        ctl->vp_kind[0] += (double)(jj + 1);
+        ctl->counter = 0;
+        return;
+    }
+    const double nw2 = ctl->wnorm2;
+    double nd2 = 0.0;
+    for (int i = 0; i <= jj; ++i) {
+        const double s = ctl->sigma[i];
+        nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
+    }
+    if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
+    ctl->vec_passes += (double)(jj + 2);
+    ctl->vp_kind[2] += (double)(jj + 2);
+    ctl->corr = 0;
+    if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
+        ctl->corr2 = 1;
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i];
+            ctl->coefC[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
+        }
+        ctl->alpha[jj] += fin[jj].x * ctl->sigma[jj];
+    } else {
+        ctl->corr2 = 0;
+        finalize_beta(ctl, jj, nw2, ctl->wg);
+    }
+    ctl->counter = 0;
+}
+
+// ---------------------------------------------------------------- linear combinations
+
+// w = src - sum_i c_i W_i, one thread per row, the terms taken in index order; w is then
+// dotted with psi0.  Plain loads, eight in flight per thread, four CTAs per SM: a pure
+// stream, which this form keeps near the HBM rate.
+template <class V, int MODE>
+__global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
 {
     KryCtl *ctl = a.ctl;
     if (ctl->done) return;
@@ -206,21 +369,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
     DotAcc<V> nrm, gacc;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * TILE, r = r0 + tid;
-        V w = VT<V>::zero();
-        if (r < D) {
-            if (src) w = src[r];
-            if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
+        const uint32_t r = tile * TILE + tid;
+        if (r >= D) continue;
+        V w = src ? src[r] : VT<V>::zero();
+        if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
 #pragma unroll 8
-                for (int i = 0; i < nvec; ++i) w = cfms(coef[i], a.W[(size_t)i * a.ldW + r], w);
-            } else {
+            for (int i = 0; i < nvec; ++i) w = cfms(coef[i], a.W[(size_t)i * a.ldW + r], w);
+        } else {
 #pragma unroll 8
-                for (int i = 0; i < nvec; ++i) w = cfms(coef[i], __ldg(a.W + (size_t)i * a.ldW + r), w);
-            }
-            out[r] = w;
-            nrm.add(w, w);
-            if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
+            for (int i = 0; i < nvec; ++i) w = cfms(coef[i], __ldg(a.W + (size_t)i * a.ldW + r), w);
         }
+        out[r] = w;
+        nrm.add(w, w);
+        if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
     }
     cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
     if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
@@ -267,77 +428,6 @@ __global__ void __launch_bounds__(NTHR, 2) k_lincomb(EvArgs<V> a, int jj)
         ctl->corr = 0;
         ctl->corr2 = 0;
         if (MODE == 2 && ctl->finishing) ctl->done = 1;
-    }
-    ctl->counter = 0;
-}
-
-// Pass C1: dots <v_i, w> of the new vector w = W_{j+1} with every earlier vector, when pass B
-// flagged them (severe cancellation, or orth_check).  Subtracts them in pass C2 when they
-// exceed eta_corr ||w||; otherwise w is accepted as it is.
-template <class V>
-__global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
-{
-    KryCtl *ctl = a.ctl;
-    if (ctl->done || jj >= ctl->m_eff || !ctl->corr) return;
-    __shared__ V wtile[TILE];
-    __shared__ double2 red[PSTRIDE];
-    __shared__ int flag;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
-    const V *w = a.W + (size_t)(jj + 1) * a.ldW;
-    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
-    DotAcc<V> acc[4];
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * TILE;
-        __syncthreads();
-        wtile[tid] = (r0 + tid < D) ? __ldg(w + r0 + tid) : VT<V>::zero();
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int iv = warp + 8 * q;
-            if (iv <= jj) {
-                const V *wi = a.W + (size_t)iv * a.ldW + r0;
-                V vv[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t rr = lane + 32 * e;
-                    vv[e] = (r0 + rr < D) ? __ldg(wi + rr) : VT<V>::zero();
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) acc[q].add(vv[e], wtile[lane + 32 * e]);
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int iv = warp + 8 * q;
-        double2 v = warp_sum(acc[q].value());
-        if (lane == 0 && iv <= jj) red[iv] = v;
-    }
-    __syncthreads();
-    double2 *fin = red;
-    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
-    if (tid != 0) return;
-    const double nw2 = ctl->wnorm2;
-    double nd2 = 0.0;
-    for (int i = 0; i <= jj; ++i) {
-        const double s = ctl->sigma[i];
-        nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
-    }
-    if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
-    ctl->vec_passes += (double)(jj + 2);
-    ctl->vp_kind[2] += (double)(jj + 2);
-    ctl->corr = 0;
-    if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
-        ctl->corr2 = 1;
-        for (int i = 0; i <= jj; ++i) {
-            const double s = ctl->sigma[i];
-            ctl->coefC[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
-        }
-        ctl->alpha[jj] += fin[jj].x * ctl->sigma[jj];
-    } else {
-        ctl->corr2 = 0;
-        finalize_beta(ctl, jj, nw2, ctl->wg);
     }
     ctl->counter = 0;
 }
@@ -471,11 +561,7 @@ size_t apply_smem(const DevBasis &b, int rl_smem, int)
     return sizeof(SmemHead) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
 }
 
-size_t passA_smem(const DevBasis &b, int rl_smem, int c64)
-{
-    return (c64 ? sizeof(float2) : sizeof(double2)) * TILE + sizeof(double2) * (PSTRIDE + NTHR / 32) +
-           sizeof(SmemHead) + 16 + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
-}
+static int dots_nr(uint32_t es) { return ring_units(0, es); }
 
 template <class K>
 static int prep_smem(K kernel, size_t smem)
@@ -513,25 +599,36 @@ int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, voi
     return KRY_OK;
 }
 
+// CTAs of the vector kernels, whole SMs times their resident CTAs: the streaming dots
+// (returned; also pass C1), the H.v of pass A (*gridH) and the updates, combine and
+// outputs (*gridB).  Also sets the kernels' shared-memory limits.
 template <class V>
-int vector_grid(const DevBasis &b, int rl_smem)
+int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 {
-    const int c64 = sizeof(V) == sizeof(float2);
-    const size_t smem = passA_smem(b, rl_smem, c64);
-    if (int rc = prep_smem(k_passA<V>, smem)) return -rc;
-    int occA = 0, occB = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_passA<V>, NTHR, smem);
+    const uint32_t es = sizeof(V);
+    const size_t smH = apply_smem(b, rl_smem, es == sizeof(float2));
+    const size_t smC = ring_bytes(dots_nr(es), es);
+    int rc = prep_smem(k_hv<V>, smH);
+    if (!rc) rc = prep_smem(k_dots<V, 0>, smC);
+    if (!rc) rc = prep_smem(k_dots<V, 1>, smC);
+    if (rc) return -rc;
+    int occA = 0, occB = 0, occH = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0>, NTHR_WS, smC);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V>, NTHR, smH);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0>, NTHR, 0);
-    int occ = std::max(1, std::min(occA, occB));
     const uint32_t ntiles = (b.D + TILE - 1) / TILE;
-    return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * occ)));
+    auto fit = [&](int occ) {
+        return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
+    };
+    *gridH = fit(occH);
+    *gridB = fit(occB);
+    return fit(occA);
 }
 
 template <class V>
-int launch_passA(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
 {
-    const size_t smem = passA_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2));
-    k_passA<V><<<grid, NTHR, smem, s>>>(a, jj);
+    k_hv<V><<<grid, NTHR, apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2)), s>>>(a, jj);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -587,19 +684,23 @@ template int launch_vecout<float2>(const VecOutArgs<float2> &, int, cudaStream_t
 template int launch_ckpt<double2>(const double2 *, double2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template <class V>
-int launch_dots(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
 {
-    k_dots<V><<<grid, NTHR, 0, s>>>(a, jj);
+    const uint32_t es = sizeof(V);
+    const int nr = dots_nr(es);
+    const size_t smem = ring_bytes(nr, es);
+    if (mode == 0) k_dots<V, 0><<<grid, NTHR_WS, smem, s>>>(a, jj, nr);
+    else k_dots<V, 1><<<grid, NTHR_WS, smem, s>>>(a, jj, nr);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
 
-template int launch_dots<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
-template int launch_dots<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
-template int vector_grid<double2>(const DevBasis &, int);
-template int vector_grid<float2>(const DevBasis &, int);
-template int launch_passA<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
-template int launch_passA<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
+template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t);
+template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t);
+template int vector_grid<double2>(const DevBasis &, int, int *, int *);
+template int vector_grid<float2>(const DevBasis &, int, int *, int *);
+template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
+template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
 template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t);
 template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t);
 

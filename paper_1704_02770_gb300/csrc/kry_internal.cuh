@@ -36,8 +36,11 @@ int cuda_fail(cudaError_t e, const char *what);
 // non-decreasing (entries of empty blocks repeat the next start), so the block of a rank
 // is found by binary search.  lolist lists the Llo-bit patterns grouped by popcount k,
 // each group ascending and starting at koff[k]; ranklo[lo] is lo's index in its group.
+// tstart[t] is the block holding rank t * TILE (one entry per tile of the vector kernels,
+// so a tile finds its first state with one load instead of a search).
 struct DevBasis {
     const uint32_t *blk;
+    const uint32_t *tstart;   // [ceil(D / TILE)]
     const uint16_t *ranklo;
     const uint16_t *lolist;
     const uint32_t *koff;   // [Llo + 2]
@@ -189,18 +192,16 @@ struct ExpArgs {
     double2 *Yout;   // nullable: combine coefficients of every output time [n_times][MMAX]
 };
 
-size_t passA_smem(const DevBasis &b, int rl_smem, int c64);
-size_t lincomb_smem(int c64);
 size_t apply_smem(const DevBasis &b, int rl_smem, int c64);
 
 // kernel launchers (kry_hv.cu)
 int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y,
                  int rl_smem, cudaStream_t s);
-template <class V> int launch_passA(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
 template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid,
                                       cudaStream_t s);
-template <class V> int launch_dots(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
-template <class V> int vector_grid(const DevBasis &b, int rl_smem);
+template <class V> int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s);
+template <class V> int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB);
 int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
 // small exponential (kry_exp.cu)
 int launch_smallexp(const ExpArgs &a, cudaStream_t s);
@@ -230,7 +231,7 @@ struct kry_ham_s {
     size_t ws_bytes;
     // cached CUDA graph of one Krylov step
     cudaGraphExec_t gexec;
-    int g_dtype, g_m, g_general, g_grid;
+    int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH;
     void *g_ws;
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
