@@ -7,7 +7,8 @@
 //
 //   k_apply_b      y = H x for all K (warp per state, lanes over k)
 //   k_passA_b      u = H v_j with all dots <v_i, u> per realisation
-//   k_lincomb_b    update / correction / combine / load with per-realisation coefficients
+//   k_lincomb_b    update / correction / combine / load with per-realisation coefficients,
+//                  and the dots of the new vector with the earlier ones (pass C1)
 //   k_reduce_b     per-realisation sum of the per-CTA partials (CTA order, deterministic)
 //                  and the scalar epilogue of each pass
 #include <cuda_runtime.h>
@@ -213,15 +214,19 @@ __global__ void __launch_bounds__(NTHR, 1) k_passA_b(EvArgsB<V> a, int jj)
 
 // ---------------------------------------------------------------- linear combinations (batched)
 
+// MODE 0: w = U - sum_i c_i W_i (pure update); 1: the correction of pass C2; 2: combine;
+// 3: load psi0; 4: the dots <W_i, W_{j+1}> of pass C1 (no update), for realisations that
+// flagged them.
 template <class V, int MODE, int KQ>
 __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
 {
     KryCtlB *ctl = a.ctl;
     if (ctl->hd.done) return;
-    if (MODE <= 1 && jj >= ctl->hd.m_run) return;
+    if ((MODE <= 1 || MODE == 4) && jj >= ctl->hd.m_run) return;
     if (MODE == 1 && !ctl->hd.corr_any) return;
+    if (MODE == 4 && !ctl->hd.dots_any) return;
     constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
-    const int nvec = (MODE == 2) ? ctl->hd.m_run : ((MODE == 3) ? 0 : jj + 1);
+    const int nvec = (MODE == 2) ? ctl->hd.m_run : ((MODE == 3 || MODE == 4) ? 0 : jj + 1);
     extern __shared__ __align__(16) unsigned char smem[];
     V *coef = (V *)smem;                          // [MMAX+1][Kp]
     V *wtile = coef + (MMAX + 1) * Kp;            // [TROWS][Kp]
@@ -234,8 +239,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
         coef[i * Kp + k] = VT<V>::from(c);
     }
     __syncthreads();
-    V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
-    const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
+    V *out = (MODE == 2 || MODE == 3) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
+    const V *src = (MODE == 0) ? a.U : (MODE == 1 || MODE == 4) ? out : (MODE == 3) ? a.G : nullptr;
     const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
     const int k = tid % Kp, g = tid / Kp;
     DotAcc<V> acc[QD];
@@ -247,20 +252,23 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
             if (r0 + rr < D && k < K) {
                 const size_t idx = (size_t)(r0 + rr) * K + k;
                 if (src) w = src[idx];
-                if (MODE == 2) {
+                if (MODE != 4) {
+                    if (MODE == 2) {
 #pragma unroll 8
-                    for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], a.W[(size_t)i * a.ldW + idx], w);
-                } else {
+                        for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], a.W[(size_t)i * a.ldW + idx], w);
+                    } else {
 #pragma unroll 8
-                    for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], __ldg(a.W + (size_t)i * a.ldW + idx), w);
+                        for (int i = 0; i < nvec; ++i)
+                            w = cfms(coef[i * Kp + k], __ldg(a.W + (size_t)i * a.ldW + idx), w);
+                    }
+                    out[idx] = w;
+                    nrm.add(w, w);
+                    if (a.G && MODE != 3) gacc.add(__ldg(a.G + idx), w);
                 }
-                out[idx] = w;
-                nrm.add(w, w);
-                if (a.G && MODE != 3) gacc.add(__ldg(a.G + idx), w);
             }
-            if (MODE == 0) wtile[rr * Kp + k] = w;
+            if (MODE == 4) wtile[rr * Kp + k] = w;
         }
-        if (MODE == 0) {
+        if (MODE == 4) {
             __syncthreads();
             if (k < K) {
 #pragma unroll
@@ -281,12 +289,13 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
         }
     }
     double2 *pc = a.part + (size_t)blockIdx.x * PSB * Kp;
-    if (MODE == 0) {
+    if (MODE == 4) {
 #pragma unroll
         for (int q = 0; q < QD; ++q) {
             const int iv = g + NG * q;
             if (iv <= jj) pc[(size_t)iv * Kp + k] = acc[q].value();
         }
+        return;
     }
     nred[g * Kp + k] = nrm.value();
     nred[(NG + g) * Kp + k] = gacc.value();
@@ -305,19 +314,20 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
 
 // ---------------------------------------------------------------- per-realisation reductions
 
-// mode: 0 pass A, 1 pass B, 2 pass C, 4 combine, 5 load of a general psi0.
+// mode: 0 pass A, 1 pass B, 3 pass C1 (dots of w), 2 pass C2 (correction), 4 combine,
+// 5 load of a general psi0.
 __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *__restrict__ part,
                                                   int grid, int Kp, int mode, int jj, int general)
 {
     KryHdrB &H = ctl->hd;
     if (H.done) return;
-    if ((mode == 0 || mode == 1 || mode == 2) && jj >= H.m_run) return;
+    if (mode <= 3 && jj >= H.m_run) return;
     const int k = blockIdx.x, tid = threadIdx.x;
-    const bool corr_pass = (mode == 2);
-    if (corr_pass && !H.corr_any) return;   // pass C did not run
+    if (mode == 2 && !H.corr_any) return;   // pass C2 did not run
+    if (mode == 3 && !H.dots_any) return;   // pass C1 did not run
     __shared__ double2 red[128];
     __shared__ double2 fin[PSB];
-    const int nd = (mode == 0 || mode == 1) ? jj + 1 : 0;
+    const int nd = (mode == 0 || mode == 3) ? jj + 1 : 0;
     auto reduce_slot = [&](int slot) {
         double2 s = make_double2(0.0, 0.0);
         for (int c = tid; c < grid; c += 128) {
@@ -335,11 +345,12 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
         __syncthreads();
     };
     for (int i = 0; i < nd; ++i) reduce_slot(i);
-    reduce_slot(SLOT_NRM);
-    if (general && mode != 0) reduce_slot(SLOT_G);
+    if (mode != 3) reduce_slot(SLOT_NRM);
+    if (general && mode != 0 && mode != 3) reduce_slot(SLOT_G);
     if (tid != 0) return;
-    const double nw2 = fin[SLOT_NRM].x;
-    const double2 gdot = (general && mode != 0) ? fin[SLOT_G] : make_double2(0.0, 0.0);
+    const double nw2 = (mode == 3) ? ctl->wnorm2[k] : fin[SLOT_NRM].x;
+    const double2 gdot = (mode == 3) ? ctl->wg[k]
+                                     : ((general && mode != 0) ? fin[SLOT_G] : make_double2(0.0, 0.0));
     auto finalize = [&](double w2, double2 gd) {
         const double bt = sqrt(w2);
         ctl->beta[jj][k] = bt;
@@ -359,6 +370,7 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
             H.vec_passes += (double)(jj + 2);
             H.vp_kind[0] += (double)(jj + 2);
             H.corr_any = 0;
+            H.dots_any = 0;
         }
         if (jj >= ctl->m_eff[k]) {
             // invariant subspace already reached: this realisation's next vectors stay zero
@@ -378,7 +390,26 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
             H.vp_kind[1] += (double)(jj + 3) + (general ? 1.0 : 0.0);
         }
         ctl->corr[k] = 0;
+        ctl->dots[k] = 0;
+        for (int i = 0; i <= jj; ++i) ctl->coefC[i][k] = make_double2(0.0, 0.0);
         if (jj >= ctl->m_eff[k]) return;
+        // One classical Gram-Schmidt pass is enough unless the projection cancelled most of
+        // u (||w|| < eta ||u||, the Daniel-Gragg-Kaufman-Stewart test); then this
+        // realisation takes the dots of w with every previous vector (pass C1).
+        if (H.verify || nw2 < H.eta_cancel * H.eta_cancel * ctl->normu2[k]) {
+            ctl->dots[k] = 1;
+            ctl->wnorm2[k] = nw2;
+            ctl->wg[k] = gdot;
+            H.dots_any = 1;
+        } else {
+            finalize(nw2, gdot);
+        }
+    } else if (mode == 3) {
+        if (k == 0) {
+            H.vec_passes += (double)(jj + 2);
+            H.vp_kind[2] += (double)(jj + 2);
+        }
+        if (!ctl->dots[k] || jj >= ctl->m_eff[k]) return;
         double nd2 = 0.0;
         for (int i = 0; i <= jj; ++i) {
             const double s = ctl->sigma[i][k];
@@ -392,10 +423,8 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
                 const double s = ctl->sigma[i][k];
                 ctl->coefC[i][k] = make_double2(fin[i].x * s * s, fin[i].y * s * s);
             }
-            for (int i = jj + 1; i <= MMAX; ++i) ctl->coefC[i][k] = make_double2(0.0, 0.0);
             ctl->alpha[jj][k] += fin[jj].x * ctl->sigma[jj][k];
         } else {
-            for (int i = 0; i <= jj; ++i) ctl->coefC[i][k] = make_double2(0.0, 0.0);
             finalize(nw2, gdot);
         }
     } else if (mode == 2) {
@@ -537,6 +566,7 @@ int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream
         case 0: if (int rc = set_smem(k_lincomb_b<V, 0, KQ>, sL)) return rc; k_lincomb_b<V, 0, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
         case 1: if (int rc = set_smem(k_lincomb_b<V, 1, KQ>, sL)) return rc; k_lincomb_b<V, 1, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
         case 2: if (int rc = set_smem(k_lincomb_b<V, 2, KQ>, sL)) return rc; k_lincomb_b<V, 2, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
+        case 4: if (int rc = set_smem(k_lincomb_b<V, 4, KQ>, sL)) return rc; k_lincomb_b<V, 4, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
         default: if (int rc = set_smem(k_lincomb_b<V, 3, KQ>, sL)) return rc; k_lincomb_b<V, 3, KQ><<<grid, NTHR, sL, s>>>(a, jj); break;
         }
     });
@@ -544,8 +574,8 @@ int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream
     return KRY_OK;
 }
 
-// mode 0..2 follow passes A..C; 4 the combine (then the shared step bookkeeping);
-// 5 the load of a general psi0.
+// mode 0, 1 follow passes A, B; 3 and 2 passes C1 and C2; 4 the combine (then the shared
+// step bookkeeping); 5 the load of a general psi0.
 int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, int mode, int jj,
                     int general, double, cudaStream_t s)
 {

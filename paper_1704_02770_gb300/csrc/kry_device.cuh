@@ -48,6 +48,7 @@ __device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a)
 }
 __device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
+__device__ __forceinline__ float2 scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
 // ---------------------------------------------------------------- dot accumulators
 // sum conj(a) b.  complex128: FP64 fused multiply-adds.  complex64: every product is
@@ -117,6 +118,22 @@ struct DotAccF2 {
         ff_pair_add(s1, c1, a, make_float2(b4.x, b4.y));
         ff_pair_add(s2, c2, a, make_float2(b4.z, b4.w));
     }
+    __device__ __forceinline__ void add2(float2 a0, float4 b0, float2 a1, float4 b1)
+    {
+        add(a0, b0);
+        add(a1, b1);
+    }
+    // b = (bx, by), broadcast per use
+    __device__ __forceinline__ void add(float2 a, float2 b)
+    {
+        ff_pair_add(s1, c1, a, make_float2(b.x, b.x));
+        ff_pair_add(s2, c2, a, make_float2(b.y, b.y));
+    }
+    __device__ __forceinline__ void add2(float2 a0, float2 b0, float2 a1, float2 b1)
+    {
+        add(a0, b0);
+        add(a1, b1);
+    }
     __device__ __forceinline__ double2 value() const
     {
         const double axbx = (double)s1.x + (double)c1.x, aybx = (double)s1.y + (double)c1.y;
@@ -131,9 +148,25 @@ template <> struct DotAcc<float2> : DotAccF {};
 
 // Streaming dots against a fixed tile y (the right operand, staged in shared memory once
 // per tile): complex64 keeps y expanded as (yx, yx, yy, yy) for the packed accumulator.
+// complex128 dots taken two elements at a time into two independent FP64 accumulators,
+// so consecutive fused multiply-adds do not wait on one another
+struct DotAccD2 {
+    DotAccD p, q;
+    __device__ __forceinline__ void add2(double2 a0, double2 b0, double2 a1, double2 b1)
+    {
+        p.add(a0, b0);
+        q.add(a1, b1);
+    }
+    __device__ __forceinline__ double2 value() const
+    {
+        const double2 x = p.value(), y = q.value();
+        return make_double2(x.x + y.x, x.y + y.y);
+    }
+};
+
 template <class V> struct TileDot;
 template <> struct TileDot<double2> {
-    using Acc = DotAccD;
+    using Acc = DotAccD2;
     using Y = double2;
     __device__ __forceinline__ static Y expand(double2 u) { return u; }
     __device__ __forceinline__ static Y zero() { return make_double2(0.0, 0.0); }
@@ -234,77 +267,6 @@ __device__ __forceinline__ V hv_row(const DevBasis &b, const DevHam &hm, const V
         acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
     return axpby(d, __ldg(x + base + off), (R)hm.halfJ, acc);
-}
-
-// The same row with the hop amplitudes requested in batches of HB: the targets of a batch
-// are formed first, then its loads are issued together, then summed (an unused slot adds
-// zero, so this suits complex64, where adds are cheap).  Bonds inside the lower part keep
-// the block (target base + ranklo[lo']); bonds inside the upper part keep the offset
-// (target blk[hi'] + off, blk staged in shared memory when blk_s is set); the bond joining
-// the halves and the ring bond take both lookups.
-template <class V, int HB>
-__device__ __forceinline__ V hv_row_batched(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
-                                            uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
-                                            const uint16_t *rl, const uint32_t *blk_s)
-{
-    using R = typename VT<V>::R;
-    const int Llo = b.Llo, L = b.L;
-    const uint32_t pos = koff_s[klo] + off;
-    const uint32_t lo = __ldg(b.lolist + pos);
-    const uint32_t s = (hi << Llo) | lo;
-    const uint32_t base = blk_s ? blk_s[hi] : __ldg(b.blk + hi);
-    const uint32_t lomask = (1u << Llo) - 1u;
-    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
-    const uint32_t anti = (s ^ (s >> 1)) & obc;
-    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
-    const int nanti = __popc(anti) + (int)wrap;
-    const R d = (R)hm.cz * (R)(hm.nbonds - 2 * nanti) + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
-    const V xd = __ldg(x + base + off);
-    V acc = VT<V>::zero();
-    auto blkv = [&](uint32_t h) { return blk_s ? blk_s[h] : __ldg(b.blk + h); };
-    // the masks keep every table index in range even for an unused slot
-    const uint32_t himask = (1u << b.Lhi) - 1u;
-    // bonds inside the lower part
-    uint32_t al = anti & ((1u << (Llo - 1)) - 1u);
-    while (al) {
-        uint32_t idx[HB];
-#pragma unroll
-        for (int c = 0; c < HB; ++c) {
-            const int p = __ffs(al) - 1;
-            al &= al - 1u;
-            idx[c] = p < 0 ? 0xffffffffu : base + rl[(lo ^ (3u << (p & 31))) & lomask];
-        }
-        V v[HB];
-#pragma unroll
-        for (int c = 0; c < HB; ++c) v[c] = idx[c] != 0xffffffffu ? __ldg(x + idx[c]) : VT<V>::zero();
-#pragma unroll
-        for (int c = 0; c < HB; ++c) acc = acc + v[c];
-    }
-    // bonds inside the upper part
-    uint32_t ah = anti >> Llo;
-    while (ah) {
-        uint32_t idx[HB];
-#pragma unroll
-        for (int c = 0; c < HB; ++c) {
-            const int q = __ffs(ah) - 1;
-            ah &= ah - 1u;
-            idx[c] = q < 0 ? 0xffffffffu : blkv((hi ^ (3u << (q & 31))) & himask) + off;
-        }
-        V v[HB];
-#pragma unroll
-        for (int c = 0; c < HB; ++c) v[c] = idx[c] != 0xffffffffu ? __ldg(x + idx[c]) : VT<V>::zero();
-#pragma unroll
-        for (int c = 0; c < HB; ++c) acc = acc + v[c];
-    }
-    // the bond joining the halves, and the ring bond (L-1, 0)
-    const bool jn = b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u);
-    const uint32_t sj = s ^ (3u << (Llo - 1)), sr = s ^ ((1u << (L - 1)) | 1u);
-    const uint32_t ij = jn ? blkv((sj >> Llo) & himask) + rl[sj & lomask] : 0u;
-    const uint32_t ir = wrap ? blkv((sr >> Llo) & himask) + rl[sr & lomask] : 0u;
-    const V vj = jn ? __ldg(x + ij) : VT<V>::zero();
-    const V vr = wrap ? __ldg(x + ir) : VT<V>::zero();
-    acc = acc + vj + vr;
-    return axpby(d, xd, (R)hm.halfJ, acc);
 }
 
 }  // namespace kry

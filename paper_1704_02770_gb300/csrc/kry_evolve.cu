@@ -360,8 +360,8 @@ int grid_for_b(const kry_ham_s *H, int dtype)
 }
 
 // One Krylov step of the batched path, in groups whose boundaries carry the profile events:
-// per Lanczos index {pass A, reduce}, {pass B, reduce}, {pass C, reduce, m_run};
-// then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
+// per Lanczos index {pass A, reduce}, {pass B, reduce}, {pass C1, reduce, pass C2, reduce,
+// m_run}; then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
 template <class V>
 int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m, int grid, int general)
 {
@@ -390,6 +390,8 @@ int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m,
         if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 0, jj, grid, cs);
         if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 1, jj, general, 0, cs);
         mark();
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 4, jj, grid, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 3, jj, general, 0, cs);
         if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 1, jj, grid, cs);
         if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 2, jj, general, 0, cs);
     }
@@ -475,6 +477,8 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     hd.tol = tol;
     hd.n_times = n_times;
     hd.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
+    hd.eta_cancel = 0.1;
+    hd.verify = H->orth_check;
     hd.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
     for (int k = 0; k < K; ++k) c->m_eff[k] = m;
     const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)K;
@@ -564,7 +568,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         st->max_orth_loss = *std::max_element(orth.begin(), orth.end());
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (7 * m + 5) + (general ? 2 : 1);
+        st->n_launches = launched * (9 * m + 5) + (general ? 2 : 1);
     }
     return KRY_OK;
 }

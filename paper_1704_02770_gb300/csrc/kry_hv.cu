@@ -127,14 +127,16 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
 // k_dots: NCW consumer warps and one producer warp
 constexpr int NCW = 8;
 constexpr int NTHR_WS = (NCW + 1) * 32;
+// ring budget of k_dots: three CTAs per SM for complex64, two for complex128
+constexpr uint32_t dots_ring_budget(uint32_t es) { return es == sizeof(float2) ? 66u * 1024u : RING_BUDGET; }
 static_assert(NCW == GV, "one consumer warp per chunk of a unit");
 
 // ---------------------------------------------------------------- pass A
 
-// u = sigma_j H W_j, written to U, with <W_j, u> (alpha_j) and ||u||^2 reduced on the way
-// (W_j[r] is read for the diagonal term anyway).  One thread per row at full occupancy:
-// the gathers of the hops are latency-bound, so as many rows as possible are kept in
-// flight; the dots with the earlier vectors are a separate stream (k_dots, mode 0).
+// u = sigma_j H W_j, written to U (pass A, part 1).  One thread per row at full occupancy
+// and nothing else: the gathers of the hops are latency-bound, so as many rows as possible
+// are kept in flight.  alpha_j, ||u||^2 and the dots with the earlier vectors are taken by
+// the streaming pass that follows (k_dots, mode 0).
 template <class V>
 __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 {
@@ -143,44 +145,20 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
     extern __shared__ __align__(16) unsigned char smem[];
     SmemHead *hd = (SmemHead *)smem;
     uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHead));
-    __shared__ double2 red[PSTRIDE];
-    __shared__ double2 wtmp[NTHR / 32];
-    __shared__ int flag;
-    const int tid = threadIdx.x;
-    if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
     stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
     __syncthreads();
     const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
-    const double sj = ctl->sigma[jj];
+    const typename VT<V>::R sj = (typename VT<V>::R)ctl->sigma[jj];
     const V *x = a.W + (size_t)jj * a.ldW;
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
-    DotAcc<V> nrm, dxu;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * TILE, r = r0 + tid;
+        const uint32_t r0 = tile * TILE, r = r0 + threadIdx.x;
         if (r < D) {
             uint32_t hi, off;
             int klo;
-            tile_unrank(a.b, hd->bsz, r0, tid, hi, off, klo);
-            const V u = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
-            a.U[r] = u;
-            nrm.add(u, u);
-            dxu.add(__ldg(x + r), u);
+            tile_unrank(a.b, hd->bsz, r0, threadIdx.x, hi, off, klo);
+            a.U[r] = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
         }
-    }
-    cta_sum_into(dxu.value(), red, 0, wtmp);
-    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
-    double2 *fin = red;
-    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
-    if (tid == 0) {
-        const double s = ctl->sigma[jj];
-        const double2 c = make_double2(fin[0].x * s, fin[0].y * s);   // <v_j, u>
-        ctl->coefA[jj] = make_double2(c.x * s, c.y * s);
-        ctl->alpha[jj] = c.x;
-        ctl->normu2 = fin[SLOT_NRM].x;
-        ctl->n_hv += 1;
-        ctl->vec_passes += 2.0;
-        ctl->vp_kind[0] += 2.0;
-        ctl->counter = 0;
     }
 }
 
@@ -190,17 +168,16 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 // registers), units 1.. carry up to GV vectors W_i, one per consumer warp.  A consumer warp
 // hands a slot back with one arrival on the slot's "empty" barrier; no CTA-wide barrier
 // is taken per unit, so the warps run ahead of one another.
-//   MODE 0 (pass A, j >= 1): y = U = sigma_j H W_j, i < j; fills coefA[0..j).
+//   MODE 0 (pass A): y = U = sigma_j H W_j, i <= j; fills coefA[0..j], alpha_j and
+//          ||u||^2 (taken by consumer warp 0 from its rows of u).
 //   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}, i <= j; measures the loss of
 //          orthogonality and sets up the subtraction of pass C2 when it exceeds eta_corr.
 template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr)
+__global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) k_dots(EvArgs<V> a, int jj, int nr)
 {
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
-    if (MODE == 0 && jj == 0) return;
     if (MODE == 1 && !ctl->corr) return;
-    using Y = typename TileDot<V>::Y;
     __shared__ double2 red[PSTRIDE];
     __shared__ int flag;
     __shared__ volatile int abort_s;
@@ -221,7 +198,7 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
     }
     __syncthreads();
     const V *y = (MODE == 0) ? a.U : a.W + (size_t)(jj + 1) * a.ldW;
-    const int nv = (MODE == 0) ? jj : jj + 1;   // vectors W_0 .. W_{nv-1}
+    const int nv = jj + 1;   // vectors W_0 .. W_j
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
     const int nch = 1 + nv, ng = 1 + (nv + GV - 1) / GV;
     const uint32_t nq = cta_tiles(ntiles) * (uint32_t)ng;
@@ -242,11 +219,12 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
         }
     } else {
         typename TileDot<V>::Acc acc[MMAX / GV];
+        DotAcc<V> nrm;
         uint32_t q = 0;
         for (uint32_t tile = blockIdx.x; tile < ntiles && !abort_s; tile += gridDim.x) {
             const uint32_t r0 = tile * TILE;
             const bool full_tile = r0 + TILE <= D;
-            Y yv[8];
+            V yv[8];
             {   // unit 0: this lane's rows of y
                 const int st = (int)(q % (uint32_t)nr);
                 if (!mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u)) { abort_s = 1; break; }
@@ -254,7 +232,8 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const uint32_t rr = lane + 32 * e;
-                    yv[e] = (full_tile || r0 + rr < D) ? TileDot<V>::expand(ys[rr]) : TileDot<V>::zero();
+                    yv[e] = (full_tile || r0 + rr < D) ? ys[rr] : VT<V>::zero();
+                    if (MODE == 0 && warp == 0) nrm.add(yv[e], yv[e]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + st);
@@ -268,13 +247,15 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
                     ok = mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u);
                     if (ok && g * GV + warp < nv) {
                         const V *wi = (const V *)R.slot(st, warp);
+                        V wv[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             const uint32_t rr = lane + 32 * e;
                             // slot rows past D hold stale data
-                            const V wv = (full_tile || r0 + rr < D) ? wi[rr] : VT<V>::zero();
-                            acc[g].add(wv, yv[e]);
+                            wv[e] = (full_tile || r0 + rr < D) ? wi[rr] : VT<V>::zero();
                         }
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) acc[g].add2(wv[e], yv[e], wv[e + 1], yv[e + 1]);
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(empty + st);
@@ -288,6 +269,10 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
             const int iv = g * GV + warp;
             double2 v = warp_sum(acc[g].value());
             if (lane == 0 && iv < nv) red[iv] = v;
+        }
+        if (MODE == 0 && warp == 0) {
+            const double2 v = warp_sum(nrm.value());
+            if (lane == 0) red[SLOT_NRM] = v;
         }
     }
     __syncthreads();
@@ -307,12 +292,17 @@ __global__ void __launch_bounds__(NTHR_WS, 2) k_dots(EvArgs<V> a, int jj, int nr
     if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
     if (tid != 0) return;
     if (MODE == 0) {
-        for (int i = 0; i < jj; ++i) {
+        for (int i = 0; i <= jj; ++i) {
             const double s = ctl->sigma[i];
-            ctl->coefA[i] = make_double2(fin[i].x * s * s, fin[i].y * s * s);   // <v_i, u> sigma_i
+            const double2 c = make_double2(fin[i].x * s, fin[i].y * s);   // <v_i, u>
+            ctl->coefA[i] = make_double2(c.x * s, c.y * s);
+            if (i == jj) ctl->alpha[jj] = c.x;
         }
-        ctl->vec_passes += (double)(jj + 1);
-        ctl->vp_kind[0] += (double)(jj + 1);
+        ctl->normu2 = fin[SLOT_NRM].x;
+        ctl->n_hv += 1;
+        // pass A streams W_j and U through k_hv (2 vectors) and U, W_0..W_j here (j + 2)
+        ctl->vec_passes += (double)(jj + 4);
+        ctl->vp_kind[0] += (double)(jj + 4);
         ctl->counter = 0;
         return;
     }
@@ -561,7 +551,7 @@ size_t apply_smem(const DevBasis &b, int rl_smem, int)
     return sizeof(SmemHead) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
 }
 
-static int dots_nr(uint32_t es) { return ring_units(0, es); }
+static int dots_nr(uint32_t es) { return ring_units(0, es, dots_ring_budget(es)); }
 
 template <class K>
 static int prep_smem(K kernel, size_t smem)

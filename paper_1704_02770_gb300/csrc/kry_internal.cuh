@@ -78,6 +78,9 @@ struct KryHdrB {   // shared scalars (copied to the host when polling)
     unsigned long long n_hv, n_steps, n_corr, n_bd;
     int K, m, m_run, corr_any, finishing, done, err;
     int n_times, next_out, next_out_new, r0;
+    // second Gram-Schmidt pass: dots_any = some realisation takes the dots of w (pass C1)
+    double eta_cancel;
+    int verify, dots_any;
 };
 struct KryCtlB {
     KryHdrB hd;
@@ -86,6 +89,9 @@ struct KryCtlB {
     double2 g[MMAX + 2][KBMAX];
     double normu2[KBMAX], beta0[KBMAX], tau_ok[KBMAX], err_k[KBMAX], orth[KBMAX];
     int m_eff[KBMAX], corr[KBMAX];
+    double wnorm2[KBMAX];   // ||w||^2 of pass B, kept for pass C1
+    double2 wg[KBMAX];      // <psi0, w> of pass B
+    int dots[KBMAX];        // this realisation takes the dots of w (pass C1)
 };
 
 template <class V>

@@ -67,15 +67,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Test the phase; a thread whose phase is not complete is suspended (it issues nothing)
+// until the phase completes or about SUSPEND_NS pass, so a waiting warp costs no issue slots.
+constexpr uint32_t SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -106,10 +109,10 @@ struct Ring {
 __host__ __device__ inline size_t ring_bytes(int nr, size_t es) { return 128 + (size_t)nr * GV * TILE * es; }
 
 // ring depth that fits `fixed` other bytes into the per-CTA budget (2..8 units)
-inline int ring_units(size_t fixed, size_t es)
+inline int ring_units(size_t fixed, size_t es, uint32_t budget = RING_BUDGET)
 {
     const size_t unit = (size_t)GV * TILE * es;
-    long long n = ((long long)RING_BUDGET - (long long)fixed - 128) / (long long)unit;
+    long long n = ((long long)budget - (long long)fixed - 128) / (long long)unit;
     if (n < 2) n = 2;
     if (n > 8) n = 8;
     return (int)n;

@@ -66,6 +66,27 @@ def test_each_realisation_matches_oracle(kry, dtype, bar):
     assert worst <= bar
 
 
+@pytest.mark.parametrize("dtype,bound", [("c128", 1e-12), ("c64", 2e-5)])
+def test_orthogonality_check_batched(kry, dtype, bound):
+    """Every realisation of a batch keeps each new Lanczos vector orthogonal to the previous
+    ones after one classical Gram-Schmidt pass: measured after every update with orth_check
+    on (every realisation takes the dots of pass C1), and the results agree with the default
+    run."""
+    L, N, K = 14, 7, 6
+    h = _fields(L, 1.5, 3, K)
+    times = workloads.log_times(12, 0.1, 30.0)
+    st = workloads.neel_state(L)
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, h)
+    tol = 1e-10 if dtype == "c128" else 1e-7
+    P0, _ = H.return_probability(st, times, tol=tol, dtype=dtype)
+    H.orth_check(True)
+    P1, st1 = H.return_probability(st, times, tol=tol, dtype=dtype)
+    H.orth_check(False)
+    print(f"[orth] batched L14 K=6 {dtype}: max |<v_i, w>|/||w|| = {st1['max_orth_loss']:.2e}")
+    assert 0.0 < st1["max_orth_loss"] <= bound
+    assert np.max(np.abs(P1 - P0)) <= (1e-12 if dtype == "c128" else 1e-6)
+
+
 def test_general_initial_states_batched(kry):
     L, N, K = 10, 5, 4
     h = _fields(L, 1.0, 9, K)

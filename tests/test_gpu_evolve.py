@@ -167,9 +167,9 @@ def test_profiling_changes_nothing_and_counts_every_kernel(kry):
     for k in ("passA", "passB", "passC"):
         assert prof[k]["launches"] == m * steps and prof[k]["ms"] > 0.0
     assert prof["combine"]["launches"] == steps
-    # algorithmic bytes of pass A: H.v reads v_j and writes u (2 vectors); the dots for
-    # j >= 1 read u and v_0..v_{j-1} (j + 1 vectors); all complex128 of length D
-    want = st1["n_krylov_steps"] * sum(2 + (j + 1 if j else 0) for j in range(m)) * B.dim * 16
+    # algorithmic bytes of pass A: H.v reads v_j and writes u (2 vectors); the dots read
+    # u and v_0..v_j (j + 2 vectors); all complex128 of length D
+    want = st1["n_krylov_steps"] * sum(j + 4 for j in range(m)) * B.dim * 16
     assert prof["passA"]["bytes"] == pytest.approx(want, rel=1e-12)
     # five kernels per Lanczos index (H.v, dots, update, C1, C2), then exponential and combine
     assert st1["n_launches"] == steps * (5 * m + 2) + 1
