@@ -6,7 +6,8 @@
 // time grid, so the step size is the smallest step every realisation accepts.
 //
 //   k_apply_b      y = H x for all K (warp per state, lanes over k)
-//   k_passA_b      u = H v_j with all dots <v_i, u> per realisation
+//   k_hv_b         u = H v_j for all K (pass A, part 1)
+//   k_dots_b       all dots <v_i, u> and ||u||^2 per realisation (pass A, part 2)
 //   k_lincomb_b    update / correction / combine / load with per-realisation coefficients,
 //                  and the dots of the new vector with the earlier ones (pass C1)
 //   k_reduce_b     per-realisation sum of the per-CTA partials (CTA order, deterministic)
@@ -132,84 +133,99 @@ __global__ void __launch_bounds__(NTHR) k_apply_b(DevBasis b, DevHam hm, int K, 
 
 // ---------------------------------------------------------------- pass A (batched)
 
+// Part 1: U[:, k] = sigma_j[k] H_k W_j[:, k] for every realisation (warp per state, lanes over
+// k), at full occupancy: nothing but the gathers.
 template <class V, int KQ>
-__global__ void __launch_bounds__(NTHR, 1) k_passA_b(EvArgsB<V> a, int jj)
+__global__ void __launch_bounds__(NTHR) k_hv_b(EvArgsB<V> a, int jj)
+{
+    using R = typename VT<V>::R;
+    KryCtlB *ctl = a.ctl;
+    if (ctl->hd.done || jj >= ctl->hd.m_run) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemHeadB *hd = (SmemHeadB *)smem;
+    uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHeadB));
+    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
+    __syncthreads();
+    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, K = a.K;
+    R sg[KQ];
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+        const int k = lane + 32 * q;
+        sg[q] = (k < K) ? (R)ctl->sigma[jj][k] : (R)0;
+    }
+    const V *x = a.W + (size_t)jj * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TROWS;
+        for (int rr = warp; rr < TROWS; rr += NTHR / 32) {
+            if (r0 + rr >= D) break;
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(a.b, hd->bsz, r0, rr, hi, off, klo);
+            V u[KQ];
+            hv_row_b<V, KQ>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u);
+#pragma unroll
+            for (int q = 0; q < KQ; ++q) {
+                const int k = lane + 32 * q;
+                if (k < K) a.U[(size_t)(r0 + rr) * K + k] = scale(u[q], sg[q]);
+            }
+        }
+    }
+}
+
+// Part 2: the dots <W_i[:, k], U[:, k]>, i <= j, and ||U[:, k]||^2 of every realisation.
+// Thread (k, g) takes column k and the vectors i = g, g + NG, ...; the rows of U of a tile
+// are loaded once and serve all of them.
+template <class V, int KQ>
+__global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
 {
     KryCtlB *ctl = a.ctl;
     if (ctl->hd.done || jj >= ctl->hd.m_run) return;
     constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
-    extern __shared__ __align__(16) unsigned char smem[];
-    V *utile = (V *)smem;                                        // [TROWS][Kp]
-    double *nred = (double *)(utile + TROWS * Kp);               // [8][Kp]
-    double *sig = nred + (NTHR / 32) * Kp;                       // [Kp]
-    SmemHeadB *hd = (SmemHeadB *)(sig + Kp);
-    uint16_t *rl_s = (uint16_t *)(hd + 1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = a.K;
-    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
-    for (int k = tid; k < Kp; k += NTHR) sig[k] = (k < K) ? ctl->sigma[jj][k] : 0.0;
-    __syncthreads();
-    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
-    const V *x = a.W + (size_t)jj * a.ldW;
+    constexpr int RH = TROWS / 2;   // rows per half tile
+    const int tid = threadIdx.x, K = a.K;
+    const int k = tid % Kp, g = tid / Kp;
     const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
-    const int kd = tid % Kp, gd = tid / Kp;   // dot phase: column kd, vectors i = gd + NG q
     DotAcc<V> acc[QD];
-    DotAcc<V> nrm[KQ];
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r0 = tile * TROWS;
-        for (int rr = warp; rr < TROWS; rr += NTHR / 32) {
-            V u[KQ];
-            if (r0 + rr < D) {
-                uint32_t hi, off;
-                int klo;
-                tile_unrank(a.b, hd->bsz, r0, rr, hi, off, klo);
-                hv_row_b<V, KQ>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u);
+    DotAcc<V> nrm;
+    if (k < K) {
+        for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const uint32_t r0 = tile * TROWS;
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) {
-                    const int k = lane + 32 * q;
-                    u[q] = scale(u[q], sig[k]);
-                    if (k < K) a.U[(size_t)(r0 + rr) * K + k] = u[q];
-                    nrm[q].add(u[q], u[q]);
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t rh = r0 + h * RH;
+                V uu[RH];
+#pragma unroll
+                for (int rr = 0; rr < RH; ++rr)
+                    uu[rr] = (rh + rr < D) ? __ldg(a.U + (size_t)(rh + rr) * K + k) : VT<V>::zero();
+                if (g == 0) {
+#pragma unroll
+                    for (int rr = 0; rr < RH; ++rr) nrm.add(uu[rr], uu[rr]);
                 }
-            } else {
 #pragma unroll
-                for (int q = 0; q < KQ; ++q) u[q] = VT<V>::zero();
-            }
+                for (int q = 0; q < QD; ++q) {
+                    const int iv = g + NG * q;
+                    if (iv <= jj) {
+                        const V *wi = a.W + (size_t)iv * a.ldW + (size_t)rh * K + k;
+                        V vv[RH];
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) utile[rr * Kp + lane + 32 * q] = u[q];
-        }
-        __syncthreads();
-        if (kd < K) {
+                        for (int rr = 0; rr < RH; ++rr)
+                            vv[rr] = (rh + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
 #pragma unroll
-            for (int q = 0; q < QD; ++q) {
-                const int iv = gd + NG * q;
-                if (iv <= jj) {
-                    const V *wi = a.W + (size_t)iv * a.ldW + (size_t)r0 * K + kd;
-                    V vv[TROWS];
-#pragma unroll
-                    for (int rr = 0; rr < TROWS; ++rr)
-                        vv[rr] = (r0 + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
-#pragma unroll
-                    for (int rr = 0; rr < TROWS; ++rr) acc[q].add(vv[rr], utile[rr * Kp + kd]);
+                        for (int rr = 0; rr < RH; ++rr) acc[q].add(vv[rr], uu[rr]);
+                    }
                 }
             }
         }
-        __syncthreads();
     }
     double2 *pc = a.part + (size_t)blockIdx.x * PSB * Kp;
 #pragma unroll
     for (int q = 0; q < QD; ++q) {
-        const int iv = gd + NG * q;
-        if (iv <= jj) pc[(size_t)iv * Kp + kd] = acc[q].value();
+        const int iv = g + NG * q;
+        if (iv <= jj) pc[(size_t)iv * Kp + k] = acc[q].value();
     }
-#pragma unroll
-    for (int q = 0; q < KQ; ++q) nred[warp * Kp + lane + 32 * q] = nrm[q].value().x;
-    __syncthreads();
-    for (int k = tid; k < Kp; k += NTHR) {
-        double s = 0.0;
-        for (int w = 0; w < NTHR / 32; ++w) s += nred[w * Kp + k];
-        pc[(size_t)SLOT_NRM * Kp + k] = make_double2(s, 0.0);
-    }
+    if (g == 0) pc[(size_t)SLOT_NRM * Kp + k] = make_double2(nrm.value().x, 0.0);
 }
 
 // ---------------------------------------------------------------- linear combinations (batched)
@@ -504,10 +520,9 @@ static int sm_count_b()
     return n;
 }
 
-static size_t passA_b_smem(const DevBasis &b, int Kp, int rl_smem, size_t es)
+static size_t hv_b_smem(const DevBasis &b, int rl_smem)
 {
-    return es * TROWS * Kp + sizeof(double) * (NTHR / 32) * Kp + sizeof(double) * Kp + sizeof(SmemHeadB) +
-           (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
+    return sizeof(SmemHeadB) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
 }
 
 static size_t lincomb_b_smem(int Kp, size_t es)
@@ -535,10 +550,9 @@ int batched_grid(const DevBasis &b, int Kp, int rl_smem)
     const size_t es = sizeof(V);
     int occ = 1;
     KRY_KQ_SWITCH(Kp, {
-        const size_t sA = passA_b_smem(b, Kp, rl_smem, es);
-        if (int rc = set_smem(k_passA_b<V, KQ>, sA)) return -rc;
+        if (int rc = set_smem(k_hv_b<V, KQ>, hv_b_smem(b, rl_smem))) return -rc;
         int o1 = 0, o2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_passA_b<V, KQ>, NTHR, sA);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_dots_b<V, KQ>, NTHR, 0);
         const size_t sL = lincomb_b_smem(Kp, es);
         if (int rc = set_smem(k_lincomb_b<V, 0, KQ>, sL)) return -rc;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lincomb_b<V, 0, KQ>, NTHR, sL);
@@ -548,11 +562,20 @@ int batched_grid(const DevBasis &b, int Kp, int rl_smem)
     return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * occ)));
 }
 
+// pass A: the H.v at full occupancy (its own grid), then the dots on the common grid
+// (their partials feed k_reduce_b)
 template <class V>
 int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
 {
-    const size_t sA = passA_b_smem(a.b, a.Kp, a.rl_smem, sizeof(V));
-    KRY_KQ_SWITCH(a.Kp, { k_passA_b<V, KQ><<<grid, NTHR, sA, s>>>(a, jj); });
+    const size_t sH = hv_b_smem(a.b, a.rl_smem);
+    const uint32_t ntiles = (a.b.D + TROWS - 1) / TROWS;
+    KRY_KQ_SWITCH(a.Kp, {
+        int oh = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oh, k_hv_b<V, KQ>, NTHR, sH);
+        const int gh = (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * std::max(1, oh))));
+        k_hv_b<V, KQ><<<gh, NTHR, sH, s>>>(a, jj);
+        k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj);
+    });
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }

@@ -350,20 +350,29 @@ Layout layout_b(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
     return l;
 }
 
-int grid_for_b(const kry_ham_s *H, int dtype)
+// CTAs of the batched dots of pass A (returned, occupancy rule) and of the update, second
+// pass and combine (*gridB: one per SM, which measured fastest for the [state][K] rows, or
+// the autotuned override).
+int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
 {
     const DevBasis &b = H->b->dev;
     const int Kp = padded_k(H->K);
     const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b)) : batched_grid<double2>(b, Kp, rl_in_smem(b));
     const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
-    return (g > 0 && ov > 0) ? ov : g;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
+    *gridB = (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(ov > 0 ? ov : sms)));
+    return g;
 }
 
 // One Krylov step of the batched path, in groups whose boundaries carry the profile events:
 // per Lanczos index {pass A, reduce}, {pass B, reduce}, {pass C1, reduce, pass C2, reduce,
 // m_run}; then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
 template <class V>
-int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m, int grid, int general)
+int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m, int grid, int gridB,
+                   int general)
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
@@ -387,19 +396,19 @@ int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m,
         rc = launch_passA_b<V>(a, jj, grid, cs);
         if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 0, jj, general, 0, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 0, jj, grid, cs);
-        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 1, jj, general, 0, cs);
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 0, jj, gridB, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, gridB, a.K, a.Kp, 1, jj, general, 0, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 4, jj, grid, cs);
-        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 3, jj, general, 0, cs);
-        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 1, jj, grid, cs);
-        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 2, jj, general, 0, cs);
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 4, jj, gridB, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, gridB, a.K, a.Kp, 3, jj, general, 0, cs);
+        if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 1, jj, gridB, cs);
+        if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, gridB, a.K, a.Kp, 2, jj, general, 0, cs);
     }
     mark();
     if (rc == KRY_OK) rc = launch_exp_b(ea, cs);
     mark();
-    if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 2, 0, grid, cs);
-    if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 4, 0, general, 0, cs);
+    if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 2, 0, gridB, cs);
+    if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, gridB, a.K, a.Kp, 4, 0, general, 0, cs);
     mark();
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -417,9 +426,10 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
 {
     const DevBasis &b = H->b->dev;
     const int K = H->K, Kp = padded_k(K);
-    const int grid = grid_for_b(H, dtype);
+    int gridB = 0;
+    const int grid = grid_for_b(H, dtype, &gridB);
     if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
-    const Layout l = layout_b(H, dtype, m, grid, n_times);
+    const Layout l = layout_b(H, dtype, m, std::max(grid, gridB), n_times);
     if (!H->ws || H->ws_bytes < l.bytes) {
         drop_graph(H);
         if (H->ws) cudaFree(H->ws);
@@ -454,12 +464,12 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     ea.K = K;
     const int gkey = 2 + (int)general;   // distinguishes batched graphs from single ones
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != gkey ||
-                     H->g_grid != grid || H->g_ws != H->ws || H->g_G != (const void *)(base + l.oP) ||
-                     (int)H->prof_ev.empty() == H->prof_on))
+                     H->g_grid != grid || H->g_gridB != gridB || H->g_ws != H->ws ||
+                     H->g_G != (const void *)(base + l.oP) || (int)H->prof_ev.empty() == H->prof_on))
         drop_graph(H);
     if (!H->gexec) {
-        if (int rc = capture_step_b<V>(H, a, ea, m, grid, (int)general)) return rc;
-        H->g_dtype = dtype; H->g_m = m; H->g_general = gkey; H->g_grid = grid;
+        if (int rc = capture_step_b<V>(H, a, ea, m, grid, gridB, (int)general)) return rc;
+        H->g_dtype = dtype; H->g_m = m; H->g_general = gkey; H->g_grid = grid; H->g_gridB = gridB;
         H->g_ws = H->ws; H->g_G = base + l.oP;
     }
     cudaEvent_t ev0, ev1;
@@ -505,8 +515,8 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
     if (general) {
         KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
-        if (int rc = launch_lincomb_b<V>(a, 3, 0, grid, s)) return rc;
-        if (int rc = launch_reduce_b(a.ctl, a.part, grid, K, Kp, 5, 0, 1, 0, s)) return rc;
+        if (int rc = launch_lincomb_b<V>(a, 3, 0, gridB, s)) return rc;
+        if (int rc = launch_reduce_b(a.ctl, a.part, gridB, K, Kp, 5, 0, 1, 0, s)) return rc;
     } else {
         KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
         if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, r0, s)) return rc;
