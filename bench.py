@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--form", default="c128", choices=["c128", "c64", "c64b"],
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
-                    help="FP64 timed region only (no mixed, e2e or CPU legs): for ncu captures")
+                    help="FP64 timed region only (no mixed, e2e or CPU legs)")
+    ap.add_argument("--ncu-case", choices=["c128", "c64"],
+                    help="one Krylov step (m = 30, one output time) of the workload, nothing else: "
+                         "a short, fixed launch sequence for ncu captures")
     a = ap.parse_args()
     if a.kernels_only:
         a.no_mixed = a.no_cpu_baseline = a.no_batched = True
@@ -138,7 +141,7 @@ def barrier(world):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kry_hv.cu", "kry_device.cuh", "kry_internal.cuh"):
+    for f in ("kry_hv.cu", "kry_device.cuh", "kry_internal.cuh", "kry_stream.cuh"):
         with open(os.path.join(ROOT, "paper_1704_02770_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -167,13 +170,14 @@ def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
 
     Per element: a complex multiply-add is 8 flops, |w|^2 is 4.  Pass A at Lanczos index j
     does the H.v row (2 flops per gathered neighbour, 10 for the diagonal term and the
-    J/2 scale) and j+1 dots; pass B does j+1 updates and j+1 second-pass dots.
+    J/2 scale), j+1 dots and ||u||^2; pass B does j+1 updates and ||w||^2 (its second
+    Gram-Schmidt pass runs only when flagged and is counted under pass C).
     The average number of neighbours is 2N(L-N)/(L-1) on a ring, 2N(L-N)/L open."""
     nb = 2.0 * N * (L - N) / ((L - 1) if pbc else L)
     if kind == "passA":
         per = sum(8 * (j + 1) + 4 + 10 + 2 * nb for j in range(m))
     elif kind == "passB":
-        per = sum(16 * (j + 1) + 4 for j in range(m))
+        per = sum(8 * (j + 1) + 4 for j in range(m))
     else:
         return 0.0
     return per * D * krylov_steps
@@ -198,8 +202,8 @@ def roofline(prof, form, D, c, L, N, clocks):
     share = {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values()) for k in KIND_NAMES}
     if form == "c128":
         # Krylov steps that did work (replays after the last output time are no-ops):
-        # recovered from the kind's algorithmic bytes, (j+2) or (j+3) vectors at index j
-        per_step = sum((j + 2) if dom == "passA" else (j + 3) for j in range(c["m"])) * D * 16
+        # recovered from the kind's algorithmic bytes, (j+4) or (j+3) vectors at index j
+        per_step = sum((j + 4) if dom == "passA" else (j + 3) for j in range(c["m"])) * D * 16
         steps = prof[dom]["bytes"] / per_step
         fl = fp64_flops(dom, D, c["m"], steps, L, N, c["pbc"])
         mhz = clocks["sm_mhz"] or 2070.0
@@ -450,9 +454,32 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}))
 
 
+def run_ncu_case(args):
+    """One Krylov step of the workload in the given precision, with no autotuning and no
+    warm-up, so that a kernel's launch index is known: per Lanczos index j the launches
+    are k_hv, k_dots (pass A), k_lincomb (pass B), k_dots, k_lincomb (pass C, no-ops unless
+    flagged), then the small exponential and the combine."""
+    import torch
+
+    import paper_1704_02770_gb300 as kry
+    import workloads
+
+    kry.load()
+    torch.cuda.set_device(0)
+    c = workloads.config(args.workload)
+    B = kry.Basis(c["L"], c["n_up"])
+    H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
+    P, st = H.return_probability(c["state"], [0.5], m=c["m"], tol=1e-7, dtype=args.ncu_case)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "workload": args.workload, "krylov_steps": st["n_krylov_steps"],
+                      "hv": st["n_hv"], "P": float(P[0])}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.ncu_case:
+        run_ncu_case(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -192,13 +192,23 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
     if (k < K) {
         for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const uint32_t r0 = tile * TROWS;
+            // rows past D are skipped by one test per half tile, not per element
+            // (a select of FP64 values occupies the FP64 pipe)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t rh = r0 + h * RH;
+                const int nr = rh >= D ? 0 : (int)min((uint32_t)RH, D - rh);
                 V uu[RH];
 #pragma unroll
-                for (int rr = 0; rr < RH; ++rr)
-                    uu[rr] = (rh + rr < D) ? __ldg(a.U + (size_t)(rh + rr) * K + k) : VT<V>::zero();
+                for (int rr = 0; rr < RH; ++rr) uu[rr] = VT<V>::zero();
+                if (nr == RH) {
+#pragma unroll
+                    for (int rr = 0; rr < RH; ++rr) uu[rr] = __ldg(a.U + (size_t)(rh + rr) * K + k);
+                } else {
+#pragma unroll
+                    for (int rr = 0; rr < RH; ++rr)
+                        if (rr < nr) uu[rr] = __ldg(a.U + (size_t)(rh + rr) * K + k);
+                }
                 if (g == 0) {
 #pragma unroll
                     for (int rr = 0; rr < RH; ++rr) nrm.add(uu[rr], uu[rr]);
@@ -210,8 +220,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
                         const V *wi = a.W + (size_t)iv * a.ldW + (size_t)rh * K + k;
                         V vv[RH];
 #pragma unroll
-                        for (int rr = 0; rr < RH; ++rr)
-                            vv[rr] = (rh + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+                        for (int rr = 0; rr < RH; ++rr) vv[rr] = VT<V>::zero();
+                        if (nr == RH) {
+#pragma unroll
+                            for (int rr = 0; rr < RH; ++rr) vv[rr] = __ldg(wi + (size_t)rr * K);
+                        } else {
+#pragma unroll
+                            for (int rr = 0; rr < RH; ++rr)
+                                if (rr < nr) vv[rr] = __ldg(wi + (size_t)rr * K);
+                        }
 #pragma unroll
                         for (int rr = 0; rr < RH; ++rr) acc[q].add(vv[rr], uu[rr]);
                     }

@@ -55,8 +55,11 @@ __global__ void __launch_bounds__(NTHR) k_apply(DevBasis b, DevHam hm, const V *
 // another), then the FGROUPS group sums are added in group order.  The summation order
 // depends only on the grid, so results are bitwise reproducible for a fixed grid.
 constexpr int FGROUPS = NTHR / PSTRIDE;   // 6
+// Only the slots [0, nlead) and, with tail set, SLOT_NRM and SLOT_G are summed; the others
+// of fin are zero.
 __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *part, KryCtl *ctl,
-                                                double2 *fin, int *flag, unsigned *counter = nullptr)
+                                                double2 *fin, int *flag, unsigned *counter = nullptr,
+                                                int nlead = PSTRIDE, bool tail = true)
 {
     __shared__ double2 gsum[FGROUPS][PSTRIDE];
     const int tid = threadIdx.x;
@@ -71,11 +74,13 @@ __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *par
     if (tid < FGROUPS * PSTRIDE) {
         const int g = tid / PSTRIDE, slot = tid - g * PSTRIDE;
         double2 s = make_double2(0.0, 0.0);
+        if (slot < nlead || (tail && (slot == SLOT_NRM || slot == SLOT_G))) {
 #pragma unroll 8
-        for (unsigned c = g; c < gridDim.x; c += FGROUPS) {
-            const double2 v = __ldcg(part + (size_t)c * PSTRIDE + slot);
-            s.x += v.x;
-            s.y += v.y;
+            for (unsigned c = g; c < gridDim.x; c += FGROUPS) {
+                const double2 v = __ldcg(part + (size_t)c * PSTRIDE + slot);
+                s.x += v.x;
+                s.y += v.y;
+            }
         }
         gsum[g][slot] = s;
     }
@@ -229,11 +234,17 @@ __global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) 
                 const int st = (int)(q % (uint32_t)nr);
                 if (!mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u)) { abort_s = 1; break; }
                 const V *ys = (const V *)R.slot(st, 0);
+                if (full_tile) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t rr = lane + 32 * e;
-                    yv[e] = (full_tile || r0 + rr < D) ? ys[rr] : VT<V>::zero();
-                    if (MODE == 0 && warp == 0) nrm.add(yv[e], yv[e]);
+                    for (int e = 0; e < 8; ++e) yv[e] = ys[lane + 32 * e];
+                } else {   // slot rows past D hold stale data
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        yv[e] = (r0 + lane + 32 * e < D) ? ys[lane + 32 * e] : VT<V>::zero();
+                }
+                if (MODE == 0 && warp == 0) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) nrm.add(yv[e], yv[e]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + st);
@@ -248,11 +259,13 @@ __global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) 
                     if (ok && g * GV + warp < nv) {
                         const V *wi = (const V *)R.slot(st, warp);
                         V wv[8];
+                        if (full_tile) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const uint32_t rr = lane + 32 * e;
-                            // slot rows past D hold stale data
-                            wv[e] = (full_tile || r0 + rr < D) ? wi[rr] : VT<V>::zero();
+                            for (int e = 0; e < 8; ++e) wv[e] = wi[lane + 32 * e];
+                        } else {   // slot rows past D hold stale data
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                wv[e] = (r0 + lane + 32 * e < D) ? wi[lane + 32 * e] : VT<V>::zero();
                         }
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) acc[g].add2(wv[e], yv[e], wv[e + 1], yv[e + 1]);
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) 
         return;
     }
     double2 *fin = red;
-    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (!finish_partials(red, a.part, ctl, fin, &flag, nullptr, nv, MODE == 0)) return;
     if (tid != 0) return;
     if (MODE == 0) {
         for (int i = 0; i <= jj; ++i) {
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
     cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
     if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
     double2 *fin = red;
-    if (!finish_partials(red, a.part, ctl, fin, &flag)) return;
+    if (!finish_partials(red, a.part, ctl, fin, &flag, nullptr, 0, true)) return;
     if (tid != 0) return;
     const double nw2 = fin[SLOT_NRM].x;
     const double2 gdot = fin[SLOT_G];
