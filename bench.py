@@ -45,7 +45,7 @@ def parse():
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs)")
-    ap.add_argument("--ncu-case", choices=["c128", "c64"],
+    ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b"],
                     help="one Krylov step (m = 30, one output time) of the workload, nothing else: "
                          "a short, fixed launch sequence for ncu captures")
     a = ap.parse_args()
@@ -458,7 +458,9 @@ def run_ncu_case(args):
     """One Krylov step of the workload in the given precision, with no autotuning and no
     warm-up, so that a kernel's launch index is known: per Lanczos index j the launches
     are k_hv, k_dots (pass A), k_lincomb (pass B), k_dots, k_lincomb (pass C, no-ops unless
-    flagged), then the small exponential and the combine."""
+    flagged), then the small exponential and the combine.  c64b: the batched K = 64
+    ensemble of L = 22 in complex64."""
+    import numpy as np
     import torch
 
     import paper_1704_02770_gb300 as kry
@@ -466,13 +468,14 @@ def run_ncu_case(args):
 
     kry.load()
     torch.cuda.set_device(0)
-    c = workloads.config(args.workload)
+    batched = args.ncu_case == "c64b"   # the K = 64 phase ensemble of L = 22
+    c = workloads.config("L22_batched_h1.5" if batched else args.workload)
     B = kry.Basis(c["L"], c["n_up"])
-    H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
-    P, st = H.return_probability(c["state"], [0.5], m=c["m"], tol=1e-7, dtype=args.ncu_case)
+    H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"] if batched else c["h"][0], pbc=c["pbc"])
+    P, st = H.return_probability(c["state"], [0.5], m=c["m"], tol=1e-7, dtype="c64" if batched else args.ncu_case)
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": args.ncu_case, "workload": args.workload, "krylov_steps": st["n_krylov_steps"],
-                      "hv": st["n_hv"], "P": float(P[0])}))
+    print(json.dumps({"ncu_case": args.ncu_case, "workload": c["name"], "krylov_steps": st["n_krylov_steps"],
+                      "hv": st["n_hv"], "P": float(np.asarray(P).ravel()[0])}))
 
 
 if __name__ == "__main__":

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kry_device.cuh"
 
@@ -182,12 +183,16 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
 {
     KryCtlB *ctl = a.ctl;
     if (ctl->hd.done || jj >= ctl->hd.m_run) return;
-    constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
+    // vectors i = g + NG q < MMAX (j <= MMAX - 1); complex64 accumulates with the packed
+    // float-float pairs while they fit the registers (K <= 64), else with the scalar pairs;
+    // complex128 in FP64
+    constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG - 1) / NG;
     constexpr int RH = TROWS / 2;   // rows per half tile
+    using Acc = typename std::conditional<sizeof(V) == sizeof(float2) && KQ <= 2, DotAccF2, DotAcc<V>>::type;
     const int tid = threadIdx.x, K = a.K;
     const int k = tid % Kp, g = tid / Kp;
     const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
-    DotAcc<V> acc[QD];
+    Acc acc[QD];
     DotAcc<V> nrm;
     if (k < K) {
         for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -561,22 +566,26 @@ static int set_smem(K_ kernel, size_t smem)
     default: { constexpr int KQ = 4; __VA_ARGS__; } break;    \
     }
 
+// CTAs of the batched dots (returned) and of the updates (*gridB): whole SMs times the
+// resident CTAs of each.
 template <class V>
-int batched_grid(const DevBasis &b, int Kp, int rl_smem)
+int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB)
 {
     const size_t es = sizeof(V);
-    int occ = 1;
+    int o1 = 1, o2 = 1;
     KRY_KQ_SWITCH(Kp, {
         if (int rc = set_smem(k_hv_b<V, KQ>, hv_b_smem(b, rl_smem))) return -rc;
-        int o1 = 0, o2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_dots_b<V, KQ>, NTHR, 0);
         const size_t sL = lincomb_b_smem(Kp, es);
         if (int rc = set_smem(k_lincomb_b<V, 0, KQ>, sL)) return -rc;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lincomb_b<V, 0, KQ>, NTHR, sL);
-        occ = std::max(1, std::min(o1, o2));
     });
     const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
-    return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * occ)));
+    auto fit = [&](int occ) {
+        return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * std::max(1, occ))));
+    };
+    *gridB = fit(o2);
+    return fit(o1);
 }
 
 // pass A: the H.v at full occupancy (its own grid), then the dots on the common grid
@@ -661,8 +670,8 @@ int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t
     return KRY_OK;
 }
 
-template int batched_grid<double2>(const DevBasis &, int, int);
-template int batched_grid<float2>(const DevBasis &, int, int);
+template int batched_grid<double2>(const DevBasis &, int, int, int *);
+template int batched_grid<float2>(const DevBasis &, int, int, int *);
 template int launch_passA_b<double2>(const EvArgsB<double2> &, int, int, cudaStream_t);
 template int launch_passA_b<float2>(const EvArgsB<float2> &, int, int, cudaStream_t);
 template int launch_lincomb_b<double2>(const EvArgsB<double2> &, int, int, int, cudaStream_t);

@@ -269,4 +269,48 @@ __device__ __forceinline__ V hv_row(const DevBasis &b, const DevHam &hm, const V
     return axpby(d, __ldg(x + base + off), (R)hm.halfJ, acc);
 }
 
+// sigma (H x)[r] for the row of hv_row, with the bond energy read from a table
+// dz[n] = (J Delta / 4)(nbonds - 2 n) and sigma folded into the two factors:
+//   sigma (d x_r + (J/2) acc) = (sigma d) x_r + (sigma J/2) acc.
+template <class V>
+__device__ __forceinline__ V hv_row_scaled(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
+                                           uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
+                                           const uint16_t *rl, const typename VT<V>::R *dz,
+                                           typename VT<V>::R sigma, typename VT<V>::R sigma_halfJ)
+{
+    using R = typename VT<V>::R;
+    const int Llo = b.Llo, L = b.L;
+    const uint32_t pos = koff_s[klo] + off;
+    const uint32_t lo = __ldg(b.lolist + pos);
+    const uint32_t s = (hi << Llo) | lo;
+    const uint32_t base = __ldg(b.blk + hi);
+    const uint32_t lomask = (1u << Llo) - 1u;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint32_t anti = (s ^ (s >> 1)) & obc;
+    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
+    const R d = dz[__popc(anti) + (int)wrap] + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
+    V acc = VT<V>::zero();
+    uint32_t a = anti & ((1u << (Llo - 1)) - 1u);          // bonds inside the lower part
+    while (a) {
+        const int p = __ffs(a) - 1;
+        a &= a - 1u;
+        acc = acc + __ldg(x + base + rl[lo ^ (3u << p)]);
+    }
+    if (b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u)) {         // bond joining the two parts
+        const uint32_t s2 = s ^ (3u << (Llo - 1));
+        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    uint32_t ah = anti >> Llo;                              // bonds inside the upper part
+    while (ah) {
+        const int q = __ffs(ah) - 1;
+        ah &= ah - 1u;
+        acc = acc + __ldg(x + __ldg(b.blk + (hi ^ (3u << q))) + off);
+    }
+    if (wrap) {                                             // ring bond (L-1, 0)
+        const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
+        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    return axpby(sigma * d, __ldg(x + base + off), sigma_halfJ, acc);
+}
+
 }  // namespace kry

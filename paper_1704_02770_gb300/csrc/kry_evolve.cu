@@ -350,20 +350,16 @@ Layout layout_b(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
     return l;
 }
 
-// CTAs of the batched dots of pass A (returned, occupancy rule) and of the update, second
-// pass and combine (*gridB: one per SM, which measured fastest for the [state][K] rows, or
-// the autotuned override).
+// CTAs of the batched dots of pass A (returned) and of the update, second pass and combine
+// (*gridB), both by the occupancy rule; an autotuned override sets *gridB.
 int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
 {
     const DevBasis &b = H->b->dev;
     const int Kp = padded_k(H->K);
-    const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b)) : batched_grid<double2>(b, Kp, rl_in_smem(b));
+    const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b), gridB)
+                                   : batched_grid<double2>(b, Kp, rl_in_smem(b), gridB);
     const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t ntiles = (b.D + TROWS - 1) / TROWS;
-    *gridB = (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(ov > 0 ? ov : sms)));
+    if (g > 0 && ov > 0) *gridB = ov;
     return g;
 }
 

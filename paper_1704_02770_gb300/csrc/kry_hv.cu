@@ -147,13 +147,17 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 {
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
+    using R = typename VT<V>::R;
     extern __shared__ __align__(16) unsigned char smem[];
     SmemHead *hd = (SmemHead *)smem;
     uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHead));
+    __shared__ R dz[64];
+    if (threadIdx.x <= (unsigned)a.b.L) dz[threadIdx.x] = (R)(a.h.cz * (double)(a.h.nbonds - 2 * (int)threadIdx.x));
     stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
     __syncthreads();
     const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
-    const typename VT<V>::R sj = (typename VT<V>::R)ctl->sigma[jj];
+    const double s = ctl->sigma[jj];
+    const R sj = (R)s, shj = (R)(s * a.h.halfJ);
     const V *x = a.W + (size_t)jj * a.ldW;
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
             uint32_t hi, off;
             int klo;
             tile_unrank(a.b, hd->bsz, r0, threadIdx.x, hi, off, klo);
-            a.U[r] = scale(hv_row<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl), sj);
+            a.U[r] = hv_row_scaled<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl, dz, sj, shj);
         }
     }
 }

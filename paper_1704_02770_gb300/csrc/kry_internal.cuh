@@ -121,7 +121,7 @@ template <class V> int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cud
 template <class V> int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream_t s);
 int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, int mode, int jj,
                     int general, double es_bytes_per_vec, cudaStream_t s);
-template <class V> int batched_grid(const DevBasis &b, int Kp, int rl_smem);
+template <class V> int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB);
 int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
                    int rl_smem, cudaStream_t s);
 int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t s);
