@@ -48,8 +48,7 @@ enum {
     KRY_ENOMEM = 2,    /* device allocation failed or exceeds the configured cap        */
     KRY_ETOL = 3,      /* no step size meets the tolerance                              */
     KRY_ETIMEOUT = 4,  /* the evolution did not finish within its step budget           */
-    KRY_ECUDA = 5      /* a CUDA runtime call failed, or a kernel's wait for a copy to  */
-                       /* shared memory ran past its 1 s limit (the kernel gave up)     */
+    KRY_ECUDA = 5      /* a CUDA runtime call failed                                    */
 };
 enum { KRY_OBC = 0, KRY_PBC = 1 };
 enum { KRY_C128 = 0, KRY_C64 = 1 };

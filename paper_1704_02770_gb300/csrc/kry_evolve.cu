@@ -294,7 +294,6 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
         if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
-        else if (hp->err == KRY_ECUDA) set_error("kry_evolve: a tile copy did not complete within its wait limit");
         else set_error("kry_evolve: initial vector has zero norm");
         return hp->err;
     }

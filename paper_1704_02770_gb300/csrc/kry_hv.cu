@@ -1,8 +1,8 @@
 // Vector kernels of the Krylov step (Sec. 2, "Krylov subspace methods"):
 //   k_apply     y = H x (matrix-free, Eq. 1)
 //   k_hv        u = sigma_j H v_j with alpha_j = <v_j, u> and ||u||^2 (pass A, part 1)
-//   k_dots      <v_i, y> for the earlier vectors, streamed through shared memory by the
-//               bulk-copy engine (pass A part 2 with y = u; pass C1 with y = w)
+//   k_dots      <v_i, y> for the Krylov vectors, a tall-skinny GEMV with plain loads
+//               (pass A part 2 with y = u; pass C1 with y = w)
 //   k_lincomb   w = src - sum_i c_i W_i with an optional second sweep of dots
 //               (MODE 0: Lanczos update + second-pass dots; 1: second-pass correction;
 //                2: combine psi = beta V y; 3: load the initial vector)
@@ -11,9 +11,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kry_device.cuh"
-#include "kry_stream.cuh"
 
 namespace kry {
 
@@ -127,15 +127,6 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
     }
 }
 
-// ---------------------------------------------------------------- tile streaming
-
-// k_dots: NCW consumer warps and one producer warp
-constexpr int NCW = 8;
-constexpr int NTHR_WS = (NCW + 1) * 32;
-// ring budget of k_dots: three CTAs per SM for complex64, two for complex128
-constexpr uint32_t dots_ring_budget(uint32_t es) { return es == sizeof(float2) ? 66u * 1024u : RING_BUDGET; }
-static_assert(NCW == GV, "one consumer warp per chunk of a unit");
-
 // ---------------------------------------------------------------- pass A
 
 // u = sigma_j H W_j, written to U (pass A, part 1).  One thread per row at full occupancy
@@ -171,140 +162,90 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
     }
 }
 
-// Dots <W_i, y> of a right-hand vector y with the earlier Krylov vectors, streamed through
-// the ring by a producer warp (warp NCW, one lane issuing the bulk copies) to NCW consumer
-// warps.  Unit 0 of a tile carries y's rows (each consumer lane keeps its eight rows in
-// registers), units 1.. carry up to GV vectors W_i, one per consumer warp.  A consumer warp
-// hands a slot back with one arrival on the slot's "empty" barrier; no CTA-wide barrier
-// is taken per unit, so the warps run ahead of one another.
-//   MODE 0 (pass A): y = U = sigma_j H W_j, i <= j; fills coefA[0..j], alpha_j and
-//          ||u||^2 (taken by consumer warp 0 from its rows of u).
-//   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}, i <= j; measures the loss of
+// Dots <W_i, y>, i <= j, of a right-hand vector y with the Krylov vectors: a tall-skinny
+// GEMV with plain loads.  The vectors are read as KC = 64 interleaved columns of rows
+// (thread k takes rows r0 + k + 64 e, so the 32 lanes of a warp load 32 consecutive rows),
+// and thread (k, g) takes the vectors i = g, g + 4, ... with one accumulator per vector,
+// so the accumulations of different vectors overlap.  The sums over the 64 columns are
+// taken in a fixed order at the end.
+//   MODE 0 (pass A): y = U = sigma_j H W_j; fills coefA[0..j], alpha_j and ||u||^2.
+//   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}; measures the loss of
 //          orthogonality and sets up the subtraction of pass C2 when it exceeds eta_corr.
 template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) k_dots(EvArgs<V> a, int jj, int nr)
+__global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
 {
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr) return;
+    constexpr int KC = 64, NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, RT = 8, TR = KC * RT;
+    using Acc = typename std::conditional<sizeof(V) == sizeof(float2), DotAccF2, DotAccD>::type;
     __shared__ double2 red[PSTRIDE];
+    __shared__ double2 wred[NTHR / 32][QD + 1];
     __shared__ int flag;
-    __shared__ volatile int abort_s;
-    __shared__ uint32_t issued_s;
-    extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *empty = (uint64_t *)(smem + 64);
-    const Ring R{(uint64_t *)smem, smem + 128, nr, (uint32_t)(TILE * sizeof(V))};
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k = tid % KC, g = tid / KC;
     if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
-    if (tid == 0) {
-        for (int i = 0; i < nr; ++i) {
-            mbar_init(R.bar + i, 1);
-            mbar_init(empty + i, NCW);
-        }
-        fence_barrier_init();
-        abort_s = 0;
-        issued_s = 0;
-    }
-    __syncthreads();
     const V *y = (MODE == 0) ? a.U : a.W + (size_t)(jj + 1) * a.ldW;
     const int nv = jj + 1;   // vectors W_0 .. W_j
-    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
-    const int nch = 1 + nv, ng = 1 + (nv + GV - 1) / GV;
-    const uint32_t nq = cta_tiles(ntiles) * (uint32_t)ng;
-    if (warp == NCW) {
-        // producer: refill slot q % nr once all consumer warps have released it
-        if (lane == 0) {
-            const V *W = a.W;
-            const size_t ldW = a.ldW;
-            auto ptr = [W, ldW, y](int c) { return c == 0 ? y : W + (size_t)(c - 1) * ldW; };
-            uint32_t q = 0;
-            for (; q < nq; ++q) {
-                const int st = (int)(q % (uint32_t)nr);
-                if (q >= (uint32_t)nr && !mbar_wait(empty + st, ((q / (uint32_t)nr) - 1u) & 1u)) abort_s = 1;
-                if (abort_s) break;
-                ring_issue<V>(R, q, ng, nch, 1, D, ptr);
-            }
-            issued_s = q;
+    const uint32_t D = a.b.D, ntiles = (D + TR - 1) / TR;
+    Acc acc[QD];
+    DotAcc<V> nrm;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * TR + k;
+        const bool full = tile * TR + TR <= D;
+        V uu[RT];
+#pragma unroll
+        for (int e = 0; e < RT; ++e) uu[e] = VT<V>::zero();
+        if (full) {
+#pragma unroll
+            for (int e = 0; e < RT; ++e) uu[e] = __ldg(y + r0 + KC * e);
+        } else {
+#pragma unroll
+            for (int e = 0; e < RT; ++e)
+                if (r0 + KC * e < D) uu[e] = __ldg(y + r0 + KC * e);
         }
-    } else {
-        typename TileDot<V>::Acc acc[MMAX / GV];
-        DotAcc<V> nrm;
-        uint32_t q = 0;
-        for (uint32_t tile = blockIdx.x; tile < ntiles && !abort_s; tile += gridDim.x) {
-            const uint32_t r0 = tile * TILE;
-            const bool full_tile = r0 + TILE <= D;
-            V yv[8];
-            {   // unit 0: this lane's rows of y
-                const int st = (int)(q % (uint32_t)nr);
-                if (!mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u)) { abort_s = 1; break; }
-                const V *ys = (const V *)R.slot(st, 0);
-                if (full_tile) {
+        if (MODE == 0 && g == 0) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) yv[e] = ys[lane + 32 * e];
-                } else {   // slot rows past D hold stale data
+            for (int e = 0; e < RT; ++e) nrm.add(uu[e], uu[e]);
+        }
 #pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        yv[e] = (r0 + lane + 32 * e < D) ? ys[lane + 32 * e] : VT<V>::zero();
+        for (int q = 0; q < QD; ++q) {
+            const int iv = g + NG * q;
+            if (iv < nv) {
+                const V *wi = a.W + (size_t)iv * a.ldW + r0;
+                V vv[RT];
+#pragma unroll
+                for (int e = 0; e < RT; ++e) vv[e] = VT<V>::zero();
+                if (full) {
+#pragma unroll
+                    for (int e = 0; e < RT; ++e) vv[e] = __ldg(wi + KC * e);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < RT; ++e)
+                        if (r0 + KC * e < D) vv[e] = __ldg(wi + KC * e);
                 }
-                if (MODE == 0 && warp == 0) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) nrm.add(yv[e], yv[e]);
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(empty + st);
-                ++q;
+                for (int e = 0; e < RT; ++e) acc[q].add(vv[e], uu[e]);
             }
-            bool ok = true;
-#pragma unroll
-            for (int g = 0; g < MMAX / GV; ++g) {
-                if (g + 1 < ng && ok) {
-                    const int st = (int)(q % (uint32_t)nr);
-                    ok = mbar_wait(R.bar + st, (q / (uint32_t)nr) & 1u);
-                    if (ok && g * GV + warp < nv) {
-                        const V *wi = (const V *)R.slot(st, warp);
-                        V wv[8];
-                        if (full_tile) {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) wv[e] = wi[lane + 32 * e];
-                        } else {   // slot rows past D hold stale data
-#pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                wv[e] = (r0 + lane + 32 * e < D) ? wi[lane + 32 * e] : VT<V>::zero();
-                        }
-#pragma unroll
-                        for (int e = 0; e < 8; e += 2) acc[g].add2(wv[e], yv[e], wv[e + 1], yv[e + 1]);
-                    }
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(empty + st);
-                    ++q;
-                }
-            }
-            if (!ok) { abort_s = 1; break; }
         }
+    }
+    // per warp: the sum over its 32 columns; then the two warps of a group, in order
 #pragma unroll
-        for (int g = 0; g < MMAX / GV; ++g) {
-            const int iv = g * GV + warp;
-            double2 v = warp_sum(acc[g].value());
-            if (lane == 0 && iv < nv) red[iv] = v;
-        }
-        if (MODE == 0 && warp == 0) {
-            const double2 v = warp_sum(nrm.value());
-            if (lane == 0) red[SLOT_NRM] = v;
-        }
+    for (int q = 0; q < QD; ++q) {
+        const double2 v = warp_sum(acc[q].value());
+        if (lane == 0) wred[warp][q] = v;
+    }
+    if (MODE == 0) {
+        const double2 v = warp_sum(nrm.value());
+        if (lane == 0) wred[warp][QD] = v;
     }
     __syncthreads();
-    if (abort_s) {   // a wait timed out: let the copies in flight land, then give up
-        if (tid == 0) {
-            const uint32_t n = issued_s;
-            for (uint32_t p = n > (uint32_t)nr ? n - (uint32_t)nr : 0u; p < n; ++p)
-                mbar_wait(R.bar + p % (uint32_t)nr, (p / (uint32_t)nr) & 1u);
-            // only the error is recorded: the host stops on it, while every kernel still
-            // running reads a consistent done flag
-            ctl->err = KRY_ECUDA;
-            __threadfence();
-        }
-        return;
+    if (tid < nv) {
+        const int gg = tid % NG, q = tid / NG;
+        red[tid] = make_double2(wred[2 * gg][q].x + wred[2 * gg + 1][q].x, wred[2 * gg][q].y + wred[2 * gg + 1][q].y);
     }
+    if (MODE == 0 && tid == 0) red[SLOT_NRM] = make_double2(wred[0][QD].x + wred[1][QD].x, 0.0);
+    __syncthreads();
     double2 *fin = red;
     if (!finish_partials(red, a.part, ctl, fin, &flag, nullptr, nv, MODE == 0)) return;
     if (tid != 0) return;
@@ -317,7 +258,6 @@ __global__ void __launch_bounds__(NTHR_WS, sizeof(V) == sizeof(float2) ? 3 : 2) 
         }
         ctl->normu2 = fin[SLOT_NRM].x;
         ctl->n_hv += 1;
-        // pass A streams W_j and U through k_hv (2 vectors) and U, W_0..W_j here (j + 2)
         ctl->vec_passes += (double)(jj + 4);
         ctl->vp_kind[0] += (double)(jj + 4);
         ctl->counter = 0;
@@ -568,7 +508,6 @@ size_t apply_smem(const DevBasis &b, int rl_smem, int)
     return sizeof(SmemHead) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);
 }
 
-static int dots_nr(uint32_t es) { return ring_units(0, es, dots_ring_budget(es)); }
 
 template <class K>
 static int prep_smem(K kernel, size_t smem)
@@ -614,13 +553,9 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 {
     const uint32_t es = sizeof(V);
     const size_t smH = apply_smem(b, rl_smem, es == sizeof(float2));
-    const size_t smC = ring_bytes(dots_nr(es), es);
-    int rc = prep_smem(k_hv<V>, smH);
-    if (!rc) rc = prep_smem(k_dots<V, 0>, smC);
-    if (!rc) rc = prep_smem(k_dots<V, 1>, smC);
-    if (rc) return -rc;
+    if (int rc = prep_smem(k_hv<V>, smH)) return -rc;
     int occA = 0, occB = 0, occH = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0>, NTHR_WS, smC);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0>, NTHR, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V>, NTHR, smH);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0>, NTHR, 0);
     const uint32_t ntiles = (b.D + TILE - 1) / TILE;
@@ -693,11 +628,8 @@ template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uin
 template <class V>
 int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
 {
-    const uint32_t es = sizeof(V);
-    const int nr = dots_nr(es);
-    const size_t smem = ring_bytes(nr, es);
-    if (mode == 0) k_dots<V, 0><<<grid, NTHR_WS, smem, s>>>(a, jj, nr);
-    else k_dots<V, 1><<<grid, NTHR_WS, smem, s>>>(a, jj, nr);
+    if (mode == 0) k_dots<V, 0><<<grid, NTHR, 0, s>>>(a, jj);
+    else k_dots<V, 1><<<grid, NTHR, 0, s>>>(a, jj);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
