@@ -163,21 +163,23 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 }
 
 // Dots <W_i, y>, i <= j, of a right-hand vector y with the Krylov vectors: a tall-skinny
-// GEMV with plain loads.  The vectors are read as KC = 64 interleaved columns of rows
-// (thread k takes rows r0 + k + 64 e, so the 32 lanes of a warp load 32 consecutive rows),
-// and thread (k, g) takes the vectors i = g, g + 4, ... with one accumulator per vector,
-// so the accumulations of different vectors overlap.  The sums over the 64 columns are
-// taken in a fixed order at the end.
+// GEMV with plain loads.  The vectors are read as KC interleaved columns of rows (thread k
+// takes rows r0 + k + KC e, so a warp loads 32 consecutive rows), and thread (k, g) takes
+// the vectors i = g, g + NG, ... with one accumulator per vector, so the accumulations of
+// different vectors overlap.  complex64: KC = 32 (a warp per group of vectors), three CTAs
+// per SM; complex128: KC = 64, two.  The sums over the columns are taken in a fixed order
+// at the end.
 //   MODE 0 (pass A): y = U = sigma_j H W_j; fills coefA[0..j], alpha_j and ||u||^2.
 //   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}; measures the loss of
 //          orthogonality and sets up the subtraction of pass C2 when it exceeds eta_corr.
 template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
+__global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_dots(EvArgs<V> a, int jj)
 {
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr) return;
-    constexpr int KC = 64, NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, RT = 8, TR = KC * RT;
+    constexpr int KC = sizeof(V) == sizeof(float2) ? 32 : 64;   // columns (rows in flight per vector)
+    constexpr int NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, RT = 8, TR = KC * RT;
     using Acc = typename std::conditional<sizeof(V) == sizeof(float2), DotAccF2, DotAccD>::type;
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wred[NTHR / 32][QD + 1];
@@ -240,11 +242,23 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
         if (lane == 0) wred[warp][QD] = v;
     }
     __syncthreads();
+    constexpr int WG = KC / 32;   // warps per group
     if (tid < nv) {
         const int gg = tid % NG, q = tid / NG;
-        red[tid] = make_double2(wred[2 * gg][q].x + wred[2 * gg + 1][q].x, wred[2 * gg][q].y + wred[2 * gg + 1][q].y);
+        double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int w = 0; w < WG; ++w) {
+            t.x += wred[WG * gg + w][q].x;
+            t.y += wred[WG * gg + w][q].y;
+        }
+        red[tid] = t;
     }
-    if (MODE == 0 && tid == 0) red[SLOT_NRM] = make_double2(wred[0][QD].x + wred[1][QD].x, 0.0);
+    if (MODE == 0 && tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < WG; ++w) t += wred[w][QD].x;
+        red[SLOT_NRM] = make_double2(t, 0.0);
+    }
     __syncthreads();
     double2 *fin = red;
     if (!finish_partials(red, a.part, ctl, fin, &flag, nullptr, nv, MODE == 0)) return;
