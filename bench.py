@@ -192,14 +192,15 @@ def roofline(prof, form, D, c, L, N, clocks):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
     dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
-    per = {k: {"ms": round(v["ms"], 3), "GBps": (v["bytes"] / (v["ms"] * 1e6)) if v["ms"] else None,
-               "launches": v["launches"]} for k, v in prof.items()}
+    per = {k: {"ms": round(prof[k]["ms"], 3),
+               "GBps": (prof[k]["bytes"] / (prof[k]["ms"] * 1e6)) if prof[k]["ms"] else None,
+               "launches": prof[k]["launches"]} for k in KIND_NAMES}
     ach = prof[dom]["bytes"] / (prof[dom]["ms"] * 1e6)
     nl = max(prof[dom]["launches"], 1)
     hbm = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
            "peak_source": "measured" if peaks else "fallback"}
     tr = ncu_traffic(dom, prof[dom]["bytes"] / nl) if form == "c128" else ncu_traffic_c64(dom, prof[dom]["bytes"] / nl)
-    share = {k: prof[k]["ms"] / sum(v["ms"] for v in prof.values()) for k in KIND_NAMES}
+    share = {k: prof[k]["ms"] / sum(prof[q]["ms"] for q in KIND_NAMES) for k in KIND_NAMES}
     if form == "c128":
         # Krylov steps that did work (replays after the last output time are no-ops):
         # recovered from the kind's algorithmic bytes, (j+4) or (j+3) vectors at index j
@@ -213,9 +214,16 @@ def roofline(prof, form, D, c, L, N, clocks):
                 "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
                 "traffic": tr, "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
-                "hbm_view": hbm, "per_kind": per, "kernel_time_share": share}
+                "hbm_view": hbm, "per_kind": per, "kernel_time_share": share,
+                "profiled_region_s": prof.get("_sec"), "timing": TIMING_NOTE}
     return dict(bound="hbm", kernel=dom, traffic=tr, algo_bytes_per_launch=prof[dom]["bytes"] / nl,
-                per_kind=per, kernel_time_share=share, **hbm)
+                per_kind=per, kernel_time_share=share, profiled_region_s=prof.get("_sec"),
+                timing=TIMING_NOTE, **hbm)
+
+
+TIMING_NOTE = ("per-kind CUDA-event times from a second timed region of the same evolutions with "
+               "event nodes captured between the kernels of the step graph; value comes from the "
+               "uninstrumented region")
 
 
 def ncu_traffic_c64(kind, algo_bytes_per_launch):
@@ -246,6 +254,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def timed(dtype, tol, profile, Hx=None, cx=None, warmup=None, steps=None):
+        """Time n_steps evolutions (the value: no instrumentation in the graph); with
+        `profile`, time them once more with CUDA event nodes captured between the kernels
+        of the step graph, for the per-kernel times of the roofline."""
         Hx = H if Hx is None else Hx
         cx = c if cx is None else cx
         n_warm = args.warmup if warmup is None else warmup
@@ -256,26 +267,35 @@ def run_ours(args):
         def evolve(dt, tl):
             return Hx.return_probability(cx["state"], cx["times"], m=cx["m"], tol=tl, dtype=dt)
 
+        def region():
+            barrier(world)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            hv = launches = 0
+            P = st = None
+            e0.record(stream)
+            for _ in range(n_steps):
+                P, st = evolve(dtype, tol)
+                hv += st["n_hv"]
+                launches += st["n_launches"]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            return e0.elapsed_time(e1) / 1e3, hv, launches, P, st
+
         for _ in range(n_warm):
             evolve(dtype, tol)
+        sec, hv, launches, P, st = region()
+        prof = None
         if profile:
             Hx.profile(True)
-        barrier(world)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        hv = launches = 0
-        P = None
-        e0.record(stream)
-        for _ in range(n_steps):
-            P, st = evolve(dtype, tol)
-            hv += st["n_hv"]
-            launches += st["n_launches"]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        prof = Hx.profile_read() if profile else None
-        Hx.profile(False)
-        return e0.elapsed_time(e1) / 1e3, hv, launches, P, st, prof
+            evolve(dtype, tol)          # captures the instrumented graph
+            Hx.profile(True)            # and drops its counts
+            sec_p, _, _, _, _ = region()
+            prof = Hx.profile_read()
+            prof["_sec"] = sec_p
+            Hx.profile(False)
+        return sec, hv, launches, P, st, prof
 
     tune = {}
     if args.kernels_only and args.form == "c64b":

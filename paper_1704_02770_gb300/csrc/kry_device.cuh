@@ -50,6 +50,18 @@ __device__ __forceinline__ double2 scale(double2 a, double s) { return make_doub
 __device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
 __device__ __forceinline__ float2 scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// ---------------------------------------------------------------- launch ordering
+
+// First statement of every kernel of the replayed step: wait until the kernel before it
+// has completed and its writes are visible (griddepcontrol.wait; it returns at once for a
+// kernel launched without programmatic dependence), then let the next kernel begin its
+// launch, so that launches overlap the tails of the kernels before them.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- dot accumulators
 // sum conj(a) b.  complex128: FP64 fused multiply-adds.  complex64: every product is
 // split exactly (p = a*b rounded, e = fma(a, b, -p)) and summed with Knuth's TwoSum into a

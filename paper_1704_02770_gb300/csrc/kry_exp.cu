@@ -156,6 +156,7 @@ __device__ double2 chebyshev_basis(ExpSmem &sm, int me, int K)
 
 __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
 {
+    pdl_begin();
     KryCtl *ctl = ea.ctl;
     if (ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -554,7 +555,7 @@ int launch_smallexp(const ExpArgs &a, cudaStream_t s)
 {
     KRY_CU(cudaFuncSetAttribute(k_smallexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ExpSmem)));
-    k_smallexp<<<1, 32, sizeof(ExpSmem), s>>>(a);
+    KRY_CU(launch_pdl(k_smallexp, 1, 32, sizeof(ExpSmem), s, a));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }

@@ -136,6 +136,7 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
 template <class V>
 __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 {
+    pdl_begin();
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     using R = typename VT<V>::R;
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 template <class V, int MODE>
 __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_dots(EvArgs<V> a, int jj)
 {
+    pdl_begin();
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr) return;
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
 template <class V, int MODE>
 __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
 {
+    pdl_begin();
     KryCtl *ctl = a.ctl;
     if (ctl->done) return;
     if (MODE <= 1 && jj >= ctl->m_eff) return;
@@ -409,6 +412,7 @@ __global__ void k_set_basis_state(V *W0, uint32_t r0)
 template <class V>
 __global__ void __launch_bounds__(NTHR) k_vecout(VecOutArgs<V> a)
 {
+    pdl_begin();
     KryCtl *ctl = a.ctl;
     if (ctl->done) return;
     const int ob = ctl->out_begin, oe = ctl->out_end, me = ctl->m_eff;
@@ -438,6 +442,7 @@ template <class V>
 __global__ void __launch_bounds__(NTHR) k_ckpt(const V *__restrict__ W0, V *__restrict__ ck, size_t ldC,
                                                KryCtl *ctl, uint32_t D)
 {
+    pdl_begin();
     if (ctl->done || ctl->ckpt_every <= 0) return;
     const long long ns = ctl->n_steps;
     if (ns % ctl->ckpt_every != 0) return;
@@ -584,7 +589,7 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
 {
-    k_hv<V><<<grid, NTHR, apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2)), s>>>(a, jj);
+    KRY_CU(launch_pdl(k_hv<V>, grid, NTHR, apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2)), s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -593,10 +598,10 @@ template <class V>
 int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
 {
     switch (mode) {
-    case 0: k_lincomb<V, 0><<<grid, NTHR, 0, s>>>(a, jj); break;
-    case 1: k_lincomb<V, 1><<<grid, NTHR, 0, s>>>(a, jj); break;
-    case 2: k_lincomb<V, 2><<<grid, NTHR, 0, s>>>(a, jj); break;
-    default: k_lincomb<V, 3><<<grid, NTHR, 0, s>>>(a, jj); break;
+    case 0: KRY_CU(launch_pdl(k_lincomb<V, 0>, grid, NTHR, 0, s, a, jj)); break;
+    case 1: KRY_CU(launch_pdl(k_lincomb<V, 1>, grid, NTHR, 0, s, a, jj)); break;
+    case 2: KRY_CU(launch_pdl(k_lincomb<V, 2>, grid, NTHR, 0, s, a, jj)); break;
+    default: KRY_CU(launch_pdl(k_lincomb<V, 3>, grid, NTHR, 0, s, a, jj)); break;
     }
     KRY_CU(cudaGetLastError());
     return KRY_OK;
@@ -613,7 +618,7 @@ int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s)
 template <class V>
 int launch_vecout(const VecOutArgs<V> &a, int grid, cudaStream_t s)
 {
-    k_vecout<V><<<grid, NTHR, 0, s>>>(a);
+    KRY_CU(launch_pdl(k_vecout<V>, grid, NTHR, 0, s, a));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -621,7 +626,7 @@ int launch_vecout(const VecOutArgs<V> &a, int grid, cudaStream_t s)
 template <class V>
 int launch_ckpt(const V *W0, V *ckpt, size_t ldC, KryCtl *ctl, uint32_t D, int grid, cudaStream_t s)
 {
-    k_ckpt<V><<<grid, NTHR, 0, s>>>(W0, ckpt, ldC, ctl, D);
+    KRY_CU(launch_pdl(k_ckpt<V>, grid, NTHR, 0, s, W0, ckpt, ldC, ctl, D));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -642,8 +647,8 @@ template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uin
 template <class V>
 int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
 {
-    if (mode == 0) k_dots<V, 0><<<grid, NTHR, 0, s>>>(a, jj);
-    else k_dots<V, 1><<<grid, NTHR, 0, s>>>(a, jj);
+    if (mode == 0) KRY_CU(launch_pdl(k_dots<V, 0>, grid, NTHR, 0, s, a, jj));
+    else KRY_CU(launch_pdl(k_dots<V, 1>, grid, NTHR, 0, s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }

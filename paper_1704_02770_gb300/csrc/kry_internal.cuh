@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdarg>
+#include <utility>
 #include <vector>
 
 #include "kry.h"
@@ -22,6 +23,26 @@ constexpr double XMAX = 50.0;  // largest tau * r (half-width) handled in one st
 
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
+
+// Launch with programmatic dependent launch allowed: the kernel may begin while the
+// kernel before it in the stream finishes, and waits for that kernel's completion
+// (griddepcontrol.wait, see pdl_begin) before reading anything it wrote.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 #define KRY_CU(call)                                                 \
     do {                                                             \
