@@ -3,9 +3,9 @@
 //   k_hv        u = sigma_j H v_j with alpha_j = <v_j, u> and ||u||^2 (pass A, part 1)
 //   k_dots      <v_i, y> for the Krylov vectors, a tall-skinny GEMV with plain loads
 //               (pass A part 2 with y = u; pass C1 with y = w)
-//   k_lincomb   w = src - sum_i c_i W_i with an optional second sweep of dots
-//               (MODE 0: Lanczos update + second-pass dots; 1: second-pass correction;
-//                2: combine psi = beta V y; 3: load the initial vector)
+//   k_lincomb   w = src - sum_i c_i W_i (MODE 0: Lanczos update, pass B; 1: the second
+//               Gram-Schmidt subtraction, pass C2; 2: combine psi = beta V y; 3: load the
+//               initial vector)
 // Every reduction ends in the last CTA to finish (ticket counter), which sums the
 // per-CTA partials in CTA order: results are bitwise reproducible for a fixed grid.
 #include <cuda_runtime.h>
@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
 
 // ---------------------------------------------------------------- linear combinations
 
-// w = src - sum_i c_i W_i, one thread per row, the terms taken in index order; w is then
-// dotted with psi0.  Plain loads, eight in flight per thread, four CTAs per SM: a pure
-// stream, which this form keeps near the HBM rate.
+// w = src - sum_i c_i W_i, the terms taken in index order; w is then dotted with psi0.
+// Plain loads, two rows per thread and eight vectors unrolled (sixteen loads in flight per
+// thread), four CTAs per SM: a pure stream, which this form keeps near the HBM rate.
 template <class V, int MODE>
 __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
 {
@@ -332,20 +332,40 @@ __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
     const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
     const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
     DotAcc<V> nrm, gacc;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t r = tile * TILE + tid;
+    // two rows per thread (r and r + TILE): sixteen loads in flight per thread
+    const uint32_t nt2 = (D + 2 * TILE - 1) / (2 * TILE);
+    for (uint32_t tile = blockIdx.x; tile < nt2; tile += gridDim.x) {
+        const uint32_t r = tile * 2 * TILE + tid, r2 = r + TILE;
         if (r >= D) continue;
+        const bool l2 = r2 < D;
+        const uint32_t q2 = l2 ? r2 : r;   // past D the second row repeats the first, unstored
         V w = src ? src[r] : VT<V>::zero();
+        V w2 = src ? src[q2] : VT<V>::zero();
         if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
 #pragma unroll 8
-            for (int i = 0; i < nvec; ++i) w = cfms(coef[i], a.W[(size_t)i * a.ldW + r], w);
+            for (int i = 0; i < nvec; ++i) {
+                const V *wi = a.W + (size_t)i * a.ldW;
+                const V x1 = wi[r], x2 = wi[q2];
+                w = cfms(coef[i], x1, w);
+                w2 = cfms(coef[i], x2, w2);
+            }
         } else {
 #pragma unroll 8
-            for (int i = 0; i < nvec; ++i) w = cfms(coef[i], __ldg(a.W + (size_t)i * a.ldW + r), w);
+            for (int i = 0; i < nvec; ++i) {
+                const V *wi = a.W + (size_t)i * a.ldW;
+                const V x1 = __ldg(wi + r), x2 = __ldg(wi + q2);
+                w = cfms(coef[i], x1, w);
+                w2 = cfms(coef[i], x2, w2);
+            }
         }
         out[r] = w;
         nrm.add(w, w);
         if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
+        if (l2) {
+            out[r2] = w2;
+            nrm.add(w2, w2);
+            if (a.G && MODE != 3) gacc.add(__ldg(a.G + r2), w2);
+        }
     }
     cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
     if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
