@@ -16,6 +16,10 @@ These are independent of the CSR construction in oracle.basis:
     det[(exp(-i h1 t))_{occ, occ}].
   * two_level_P: L = 2, N = 1 is a two-level system with coupling J/2 and detuning
     h_1 - h_2: P = 1 - J^2/(J^2+d^2) sin^2(sqrt(J^2+d^2) t / 2).
+  * autocorrelation_dense: the temporal autocorrelation function of Sec. 4,
+    C(t) = (1/t) int_0^t P(t') dt', from the same eigendecomposition.  With
+    p_a = |<a|psi0>|^2, P(t') = sum_{a,b} p_a p_b cos((E_a - E_b) t'), so
+    int_0^t P = sum_{a,b} p_a p_b sin((E_a - E_b) t) / (E_a - E_b)   (= t when E_a = E_b).
 """
 from __future__ import annotations
 
@@ -70,6 +74,24 @@ def return_probability_dense(H: np.ndarray, psi0: np.ndarray, times) -> np.ndarr
     t = np.asarray(times, dtype=np.float64)
     A = (w[None, :] * np.exp(-1j * np.outer(t, E))).sum(axis=1)
     return np.abs(A) ** 2
+
+
+def autocorrelation_dense(H: np.ndarray, psi0: np.ndarray, times) -> np.ndarray:
+    """C(t) = (1/t) int_0^t P(t') dt' (Sec. 4, temporal autocorrelation), exactly from the
+    eigendecomposition; C(0) = 1.  O(D^2) memory per time: meant for small sectors."""
+    E, U = np.linalg.eigh(H)
+    w = np.abs(U.conj().T @ psi0) ** 2
+    om = E[:, None] - E[None, :]
+    ww = w[:, None] * w[None, :]
+    out = []
+    for t in np.asarray(times, dtype=np.float64):
+        if t == 0.0:
+            out.append(1.0)
+            continue
+        # sin(om t)/om, with its limit t where om = 0 (np.sinc(x) = sin(pi x)/(pi x))
+        s = t * np.sinc(om * t / np.pi)
+        out.append(float((ww * s).sum()) / t)
+    return np.array(out)
 
 
 def evolve_dense(H: np.ndarray, psi0: np.ndarray, t: float) -> np.ndarray:
