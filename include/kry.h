@@ -118,6 +118,17 @@ int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const doub
                            int n_times, int m, double tol, double *P_out,
                            kry_stats *stats, void *stream);
 
+/* Temporal autocorrelation (Sec. 4): C(t) = (1/t) int_0^t P(t') dt' with P of Eq. SP, for
+ * psi0 = the basis state psi0_state and a single-realisation Hamiltonian (K = 1; KRY_EINVAL
+ * otherwise).  The integral is accumulated over the Krylov steps of the same evolution that
+ * gives P: each step's share is a 64-point Gauss-Legendre quadrature of P on the step's small
+ * exponential, so C carries P's error budget tol plus a quadrature error far below it for
+ * step lengths the error control accepts.  C_out: host [n_times], C_out[o] = C(times[o]),
+ * C(0) = 1.  P_out: host [n_times] (required).  Other arguments as kry_return_probability. */
+int kry_autocorrelation(kry_ham H, int dtype, uint64_t psi0_state, const double *times,
+                        int n_times, int m, double tol, double *C_out, double *P_out,
+                        kry_stats *stats, void *stream);
+
 /* Gradient of the return probability of Eq. SP with respect to the on-site fields and to
  * Delta, for psi0 = the basis state psi0_state and one time t >= 0 (a single-realisation
  * Hamiltonian, K = 1; complex128).  With psi(s) = exp(-iHs) psi0 and the costate

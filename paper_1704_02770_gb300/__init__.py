@@ -46,6 +46,8 @@ SIGNATURES = {
     "kry_evolve": (_i, [_vp, _i, _vp, _dp, _i, _i, _d, _vp, _dp, ctypes.POINTER(Stats), _vp]),
     "kry_return_probability": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp,
                                     ctypes.POINTER(Stats), _vp]),
+    "kry_autocorrelation": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp, _dp,
+                                 ctypes.POINTER(Stats), _vp]),
     "kry_grad": (_i, [_vp, ctypes.c_uint64, _d, _i, _d, _i, _dp, _dp, _dp, ctypes.POINTER(Stats), _vp]),
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
@@ -196,6 +198,20 @@ class Hamiltonian:
         _check(load().kry_return_probability(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                              P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
+
+    def autocorrelation(self, state: int, times, m: int = 30, tol: float = 1e-10,
+                        dtype: str = "c128", stream=None):
+        """C(t) = (1/t) int_0^t P (Sec. 4) and P(t) at `times` from one evolution (K = 1)."""
+        import numpy as np
+        t, tp = _host_doubles(times)
+        C = np.zeros(t.size)
+        P = np.zeros(t.size)
+        st = Stats()
+        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        _check(load().kry_autocorrelation(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
+                                          C.ctypes.data_as(_dp), P.ctypes.data_as(_dp), ctypes.byref(st),
+                                          _stream(stream)))
+        return C, P, st.as_dict()
 
     def autotune(self, state: int, t_probe: float, dtype: str = "c128", m: int = 30, reps: int = 2,
                  cache: str | None = None, stream=None):

@@ -37,8 +37,10 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int rl_in_smem(const DevBasis &b) { return b.Llo <= 15 ? 1 : 0; }
 
 struct Layout {
-    size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, oY, bytes;
+    size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, oY, oC, oGL, bytes;
 };
+
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);   // (adjoint section)
 
 Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
 {
@@ -54,7 +56,9 @@ Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
     l.oTimes = round_up(l.oCtl + sizeof(KryCtl), 256);
     l.oP = round_up(l.oTimes + sizeof(double) * (size_t)n_times, 256);
     l.oY = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
-    l.bytes = round_up(l.oY + sizeof(double2) * MMAX * (size_t)n_times, 256);
+    l.oC = round_up(l.oY + sizeof(double2) * MMAX * (size_t)n_times, 256);
+    l.oGL = round_up(l.oC + sizeof(double) * (size_t)n_times, 256);
+    l.bytes = round_up(l.oGL + sizeof(double) * 2 * NGL, 256);
     return l;
 }
 
@@ -68,6 +72,7 @@ struct EvOpts {
     int ckpt_every = 0, ckpt_cap = 0;
     int n_ckpt = 0;            // out
     double ckpt_t[64] = {};    // out
+    double *C_out = nullptr;   // host [n_times]: temporal autocorrelation C(t_o)
 };
 
 // CTAs of the streaming dots (returned), of the H.v (*gridH) and of the updates (*gridB);
@@ -195,13 +200,24 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     ea.ldW = l.ldW;
     ea.c64 = dtype == KRY_C64;
     ea.Yout = (opt && opt->vec_out) ? (double2 *)(base + l.oY) : nullptr;
+    const int want_C = (opt && opt->C_out) ? 1 : 0;
+    if (want_C) {
+        static std::vector<double> glx, glw;
+        if (glx.empty()) gauss_legendre(NGL, glx, glw);
+        KRY_CU(cudaMemcpyAsync(base + l.oGL, glx.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
+        KRY_CU(cudaMemcpyAsync(base + l.oGL + sizeof(double) * NGL, glw.data(), sizeof(double) * NGL,
+                               cudaMemcpyHostToDevice, s));
+        ea.C = (double *)(base + l.oC);
+        ea.glx = (const double *)(base + l.oGL);
+        ea.glw = ea.glx + NGL;
+    }
     const void *vkey = opt ? opt->vec_out : nullptr, *ckey = opt ? opt->ckpt : nullptr;
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
                      H->g_grid != grid || H->g_gridB != gridB || H->g_gridH != gridH || H->g_ws != H->ws ||
                      H->g_G != (const void *)(base + l.oP) ||
                      H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
-                     H->g_vec != vkey || H->g_ck != ckey ||
+                     H->g_vec != vkey || H->g_ck != ckey || H->g_C != want_C ||
                      (opt && (H->g_ldo != opt->ldOut || H->g_ldc != opt->ldC))))
         drop_graph(H);
     if (!H->gexec) {
@@ -209,7 +225,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid; H->g_gridB = gridB;
         H->g_gridH = gridH;
         H->g_ws = H->ws; H->g_G = base + l.oP;
-        H->g_vec = vkey; H->g_ck = ckey;
+        H->g_vec = vkey; H->g_ck = ckey; H->g_C = want_C;
         H->g_ldo = opt ? opt->ldOut : 0;
         H->g_ldc = opt ? opt->ldC : 0;
     }
@@ -298,6 +314,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         return hp->err;
     }
     KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * H->K, cudaMemcpyDeviceToHost, s));
+    if (want_C) KRY_CU(cudaMemcpyAsync(opt->C_out, ea.C, sizeof(double) * n_times, cudaMemcpyDeviceToHost, s));
     if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
     KRY_CU(cudaStreamSynchronize(s));
     float ms = 0.f;
@@ -679,6 +696,31 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
     return H->K > 1
                ? evolve_bt<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
                : evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+}
+
+// Temporal autocorrelation (Sec. 4): C(t) = (1/t) int_0^t P(t') dt' at the output times,
+// from the same evolution as P (the small exponential integrates P over each step of the
+// dense output by Gauss-Legendre quadrature).  Single realisation (K = 1).
+extern "C" int kry_autocorrelation(kry_ham H, int dtype, uint64_t psi0_state, const double *times, int n_times,
+                                   int m, double tol, double *C_out, double *P_out, kry_stats *stats,
+                                   void *stream)
+{
+    if (!C_out) { set_error("kry_autocorrelation: C_out is NULL"); return KRY_EINVAL; }
+    if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
+    if (H->K != 1) { set_error("kry_autocorrelation: needs a single realisation (K = 1)"); return KRY_EINVAL; }
+    const int L = H->b->L;
+    if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
+        set_error("kry_autocorrelation: state is not in the (L=%d, N=%d) sector", L, H->b->N);
+        return KRY_EINVAL;
+    }
+    EvOpts opt;
+    opt.C_out = C_out;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == KRY_C64)
+        return evolve_t<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                                &opt);
+    return evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                             &opt);
 }
 
 // ---------------------------------------------------------------- adjoint gradient

@@ -154,6 +154,45 @@ __device__ double2 chebyshev_basis(ExpSmem &sm, int me, int K)
     return make_double2(c, r);
 }
 
+// <psi0|psi(t_now + tp)> from the expansion of the step (one Bessel sequence into J).
+__device__ double2 step_readout(const ExpSmem &sm, double tp, double c, double r, int K, double beta0,
+                                double *J)
+{
+    bessel_seq(tp * r, K, J);
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k <= K; ++k) {
+        const double t = J[k] * (k == 0 ? 1.0 : 2.0);
+        const double2 G = sm.gk[k];
+        // w_k G_k with w_k = (-i)^k
+        switch (k & 3) {
+        case 0: re += t * G.x; im += t * G.y; break;
+        case 1: re += t * G.y; im -= t * G.x; break;
+        case 2: re -= t * G.x; im -= t * G.y; break;
+        default: re -= t * G.y; im += t * G.x; break;
+        }
+    }
+    double sn, cs;
+    sincos(tp * c, &sn, &cs);
+    return cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
+}
+
+// int_{t_now}^{t_now + s} P(t') dt' by NGL-point Gauss-Legendre on the step's expansion
+// (warp-collective: every lane passes the same s and gets the sum).  P is an entire
+// function of t' whose frequencies are bounded by the half-width r, and s r <= XMAX = 50,
+// so 64 nodes integrate it to rounding.
+__device__ double step_integral(const ExpSmem &sm, const ExpArgs &ea, double s, double c, double r, int K,
+                                double beta0, double *J)
+{
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < NGL; q += 32) {
+        const double2 A = step_readout(sm, 0.5 * s * (1.0 + ea.glx[q]), c, r, K, beta0, J);
+        acc += ea.glw[q] * (A.x * A.x + A.y * A.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return 0.5 * s * acc;
+}
+
 __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
 {
     pdl_begin();
@@ -272,22 +311,7 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
         const unsigned mk = __ballot_sync(0xffffffffu, in);
         const int cnt = __popc(mk & ~(mk + 1u));   // leading run of lanes (times are sorted)
         if (lane < cnt) {
-            bessel_seq(tp * r, K, myJ);
-            double re = 0.0, im = 0.0;
-            for (int k = 0; k <= K; ++k) {
-                const double t = myJ[k] * (k == 0 ? 1.0 : 2.0);
-                const double2 G = sm.gk[k];
-                // w_k G_k with w_k = (-i)^k
-                switch (k & 3) {
-                case 0: re += t * G.x; im += t * G.y; break;
-                case 1: re += t * G.y; im -= t * G.x; break;
-                case 2: re -= t * G.x; im -= t * G.y; break;
-                default: re -= t * G.y; im += t * G.x; break;
-                }
-            }
-            double sn, cs;
-            sincos(tp * c, &sn, &cs);
-            const double2 A = cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
+            const double2 A = step_readout(sm, tp, c, r, K, beta0, myJ);
             ea.P[o] = A.x * A.x + A.y * A.y;
         }
         if (ea.Yout) {
@@ -309,6 +333,23 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
         }
         next += cnt;
         if (cnt < 32) break;
+    }
+    if (ea.C) {
+        // temporal autocorrelation (Sec. 4): C(t_o) = (int_0^{t_o} P) / t_o for the output
+        // times of this step, and the running integral over the whole step
+        __syncwarp();
+        const double pint = ctl->pint;
+        for (int o = ctl->next_out; o < next; ++o) {
+            const double to = ea.times[o];
+            const double s = fmax(to - t_now, 0.0);
+            const double I = step_integral(sm, ea, s, c, r, K, beta0, myJ);
+            if (lane == 0) ea.C[o] = to > 0.0 ? (pint + I) / to : 1.0;
+        }
+        if (!last) {
+            const double I = step_integral(sm, ea, tau, c, r, K, beta0, myJ);
+            if (lane == 0) ctl->pint = pint + I;
+        }
+        __syncwarp();
     }
     if (lane == 0) {
         ctl->out_begin = ctl->next_out;

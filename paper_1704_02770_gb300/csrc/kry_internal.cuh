@@ -174,6 +174,7 @@ struct KryCtl {
     int out_begin, out_end;
     int ckpt_every, n_ckpt, ckpt_cap;
     double ckpt_t[64];
+    double pint;               // int_0^t_now P(t') dt' (temporal autocorrelation)
 };
 
 // Dense output of whole vectors: psi(t_o) = sum_j Yout[o][j] W_j, written to out + o * ldOut.
@@ -217,7 +218,10 @@ struct ExpArgs {
     size_t ldW;
     int c64;
     double2 *Yout;   // nullable: combine coefficients of every output time [n_times][MMAX]
+    double *C;       // nullable: temporal autocorrelation C(t_o) of every output time
+    const double *glx, *glw;   // NGL-point Gauss-Legendre nodes and weights on [-1, 1] (with C)
 };
+constexpr int NGL = 64;   // Gauss-Legendre nodes of the per-step integral of P
 
 size_t apply_smem(const DevBasis &b, int rl_smem, int c64);
 
@@ -262,6 +266,7 @@ struct kry_ham_s {
     void *g_ws;
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
+    int g_C;                    // the graph integrates P for C(t)
     size_t g_ldo, g_ldc;
     int grid_override[2];       // per precision: CTAs of the vector kernels (0 = occupancy rule)
     int orth_check;             // measure <v_i, w> after every Lanczos update

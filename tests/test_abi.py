@@ -54,6 +54,10 @@ def test_argument_validation_without_gpu(lib):
     t = (ctypes.c_double * 2)(0.0, 1.0)
     P = (ctypes.c_double * 2)()
     assert lib.kry_return_probability(None, 0, 3, t, 2, 30, 1e-10, P, None, None) == k.KRY_EINVAL
+    C = (ctypes.c_double * 2)()
+    assert lib.kry_autocorrelation(None, 0, 3, t, 2, 30, 1e-10, C, P, None, None) == k.KRY_EINVAL
+    assert lib.kry_autocorrelation(None, 0, 3, t, 2, 30, 1e-10, None, P, None, None) == k.KRY_EINVAL
+    assert b"C_out" in lib.kry_last_error()
     assert lib.kry_tridiag_expv(None, None, 0, 0.0, 0.0, None, None, None) == k.KRY_EINVAL
     assert lib.kry_workspace_size(None, 0, 30) == -1
     assert lib.kry_basis_destroy(None) == k.KRY_OK
