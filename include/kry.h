@@ -119,15 +119,31 @@ int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state, const doub
                            kry_stats *stats, void *stream);
 
 /* Temporal autocorrelation (Sec. 4): C(t) = (1/t) int_0^t P(t') dt' with P of Eq. SP, for
- * psi0 = the basis state psi0_state and a single-realisation Hamiltonian (K = 1; KRY_EINVAL
- * otherwise).  The integral is accumulated over the Krylov steps of the same evolution that
- * gives P: each step's share is a 64-point Gauss-Legendre quadrature of P on the step's small
- * exponential, so C carries P's error budget tol plus a quadrature error far below it for
- * step lengths the error control accepts.  C_out: host [n_times], C_out[o] = C(times[o]),
- * C(0) = 1.  P_out: host [n_times] (required).  Other arguments as kry_return_probability. */
+ * psi0 = the basis state psi0_state in every realisation.  The integral is accumulated over
+ * the Krylov steps of the same evolution that gives P: each step's share is a 64-point
+ * Gauss-Legendre quadrature of P on the step's small exponential, so C carries P's error
+ * budget tol plus a quadrature error far below it for the step lengths the error control
+ * accepts.  C_out: host [n_times][K], C_out[o*K+k] = C_k(times[o]), C(0) = 1 (required).
+ * P_out: host [n_times][K] (required).  Other arguments as kry_return_probability. */
 int kry_autocorrelation(kry_ham H, int dtype, uint64_t psi0_state, const double *times,
                         int n_times, int m, double tol, double *C_out, double *P_out,
                         kry_stats *stats, void *stream);
+
+/* Power-law decay exponent (Sec. 4): the least-squares fit log C = log a - gamma log t over
+ * the n points (t[i], C[i]) with t_min <= t[i] <= t_max (host arrays, e.g. the output of
+ * kry_autocorrelation).  Host arithmetic only; no device is touched.  Returns KRY_EINVAL
+ * when fewer than two distinct times lie in the window or C <= 0 there.  log_a nullable. */
+int kry_decay_exponent(const double *t, const double *C, int n, double t_min, double t_max,
+                       double *gamma, double *log_a);
+
+/* Ensembles of initial states (Sec. 2 disorder layers, Sec. 4 random initial states):
+ * realisation k starts from the basis state psi0_states[k] (host [K], each in the sector,
+ * KRY_EINVAL otherwise) and evolves under its own fields h_k.  P_out: host [n_times][K]
+ * (required); C_out: host [n_times][K] temporal autocorrelations, or NULL to skip them.
+ * K > 1 runs the batched path (one step size for all realisations, each within tol). */
+int kry_return_probability_states(kry_ham H, int dtype, const uint64_t *psi0_states,
+                                  const double *times, int n_times, int m, double tol,
+                                  double *P_out, double *C_out, kry_stats *stats, void *stream);
 
 /* Gradient of the return probability of Eq. SP with respect to the on-site fields and to
  * Delta, for psi0 = the basis state psi0_state and one time t >= 0 (a single-realisation

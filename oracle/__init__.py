@@ -14,6 +14,7 @@ Modules:
   dense    -- dense references for small sectors (Kronecker-product H, eigh, free
               fermions, two-level formula)
   gradient -- dense Daleckii-Krein gradient of P(t) and finite differences
+  analysis -- least-squares power-law exponent gamma of C(t) (Sec. 4)
 
 Parity status of each function is stated in its own docstring ("pinned by ...").
 """

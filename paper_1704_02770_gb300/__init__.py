@@ -48,6 +48,9 @@ SIGNATURES = {
                                     ctypes.POINTER(Stats), _vp]),
     "kry_autocorrelation": (_i, [_vp, _i, ctypes.c_uint64, _dp, _i, _i, _d, _dp, _dp,
                                  ctypes.POINTER(Stats), _vp]),
+    "kry_return_probability_states": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_uint64), _dp, _i, _i, _d, _dp,
+                                           _dp, ctypes.POINTER(Stats), _vp]),
+    "kry_decay_exponent": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp]),
     "kry_grad": (_i, [_vp, ctypes.c_uint64, _d, _i, _d, _i, _dp, _dp, _dp, ctypes.POINTER(Stats), _vp]),
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
@@ -201,17 +204,40 @@ class Hamiltonian:
 
     def autocorrelation(self, state: int, times, m: int = 30, tol: float = 1e-10,
                         dtype: str = "c128", stream=None):
-        """C(t) = (1/t) int_0^t P (Sec. 4) and P(t) at `times` from one evolution (K = 1)."""
+        """C(t) = (1/t) int_0^t P (Sec. 4) and P(t) at `times` from one evolution; arrays of
+        shape [n_times] for K = 1, else [n_times][K]."""
         import numpy as np
         t, tp = _host_doubles(times)
-        C = np.zeros(t.size)
-        P = np.zeros(t.size)
+        C = np.zeros(t.size * self.K)
+        P = np.zeros(t.size * self.K)
         st = Stats()
         code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
         _check(load().kry_autocorrelation(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                           C.ctypes.data_as(_dp), P.ctypes.data_as(_dp), ctypes.byref(st),
                                           _stream(stream)))
+        if self.K > 1:
+            C, P = C.reshape(t.size, self.K), P.reshape(t.size, self.K)
         return C, P, st.as_dict()
+
+    def return_probability_states(self, states, times, m: int = 30, tol: float = 1e-10,
+                                  dtype: str = "c128", autocorrelation: bool = False, stream=None):
+        """P (and C when `autocorrelation`) with realisation k started from basis state
+        states[k]: arrays [n_times][K] (kry_return_probability_states)."""
+        import numpy as np
+        s = np.ascontiguousarray(np.asarray(states, dtype=np.uint64).ravel())
+        if s.size != self.K:
+            raise ValueError(f"need one initial state per realisation ({self.K}), got {s.size}")
+        t, tp = _host_doubles(times)
+        P = np.zeros(t.size * self.K)
+        C = np.zeros(t.size * self.K) if autocorrelation else None
+        st = Stats()
+        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        _check(load().kry_return_probability_states(
+            self._h, code, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), tp, t.size, m, tol,
+            P.ctypes.data_as(_dp), C.ctypes.data_as(_dp) if C is not None else None, ctypes.byref(st),
+            _stream(stream)))
+        P = P.reshape(t.size, self.K)
+        return (P, C.reshape(t.size, self.K), st.as_dict()) if C is not None else (P, st.as_dict())
 
     def autotune(self, state: int, t_probe: float, dtype: str = "c128", m: int = 30, reps: int = 2,
                  cache: str | None = None, stream=None):
@@ -302,6 +328,17 @@ def tridiag_expv(alpha, beta, h: float, tau: float, stream=None):
     _check(load().kry_tridiag_expv(ap, bp, a.size, float(h), float(tau), y.ctypes.data_as(_dp),
                                    err.ctypes.data_as(_dp), _stream(stream)))
     return y[0::2] + 1j * y[1::2], float(err[0])
+
+
+def decay_exponent(times, C, t_min: float, t_max: float):
+    """(gamma, log a) of the fit C(t) ~ a t^-gamma over t_min <= t <= t_max (kry_decay_exponent)."""
+    t, tp = _host_doubles(times)
+    c, cp = _host_doubles(C)
+    if c.size != t.size:
+        raise ValueError("times and C differ in length")
+    g, la = ctypes.c_double(), ctypes.c_double()
+    _check(load().kry_decay_exponent(tp, cp, t.size, float(t_min), float(t_max), ctypes.byref(g), ctypes.byref(la)))
+    return g.value, la.value
 
 
 def _return_probability_fn():

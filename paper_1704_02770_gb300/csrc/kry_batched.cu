@@ -517,14 +517,15 @@ __global__ void k_mrun_b(KryCtlB *ctl)
     H.m_run = mr;
 }
 
+// psi0_k = e_{r0_k}: each realisation starts from its own basis state
 template <class V>
-__global__ void k_set_basis_state_b(V *W0, int K, uint32_t r0)
+__global__ void k_set_basis_state_b(V *W0, int K, const KryCtlB *ctl)
 {
     const int k = threadIdx.x;
     if (k < K) {
         V one = VT<V>::zero();
         one.x = 1;
-        W0[(size_t)r0 * K + k] = one;
+        W0[(size_t)ctl->r0k[k] * K + k] = one;
     }
 }
 
@@ -662,10 +663,10 @@ int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const voi
     return KRY_OK;
 }
 
-int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t s)
+int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s)
 {
-    if (c64) k_set_basis_state_b<float2><<<1, KBMAX, 0, s>>>((float2 *)W0, K, r0);
-    else k_set_basis_state_b<double2><<<1, KBMAX, 0, s>>>((double2 *)W0, K, r0);
+    if (c64) k_set_basis_state_b<float2><<<1, KBMAX, 0, s>>>((float2 *)W0, K, ctl);
+    else k_set_basis_state_b<double2><<<1, KBMAX, 0, s>>>((double2 *)W0, K, ctl);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }

@@ -42,6 +42,17 @@ struct Layout {
 
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);   // (adjoint section)
 
+// Upload the NGL Gauss-Legendre nodes and weights of the per-step integral of P (temporal
+// autocorrelation) to dst = [nodes | weights].
+int upload_gl(char *dst, cudaStream_t s)
+{
+    static std::vector<double> glx, glw;
+    if (glx.empty()) gauss_legendre(NGL, glx, glw);
+    KRY_CU(cudaMemcpyAsync(dst, glx.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
+    KRY_CU(cudaMemcpyAsync(dst + sizeof(double) * NGL, glw.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
+    return KRY_OK;
+}
+
 Layout layout(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
 {
     Layout l{};
@@ -202,11 +213,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     ea.Yout = (opt && opt->vec_out) ? (double2 *)(base + l.oY) : nullptr;
     const int want_C = (opt && opt->C_out) ? 1 : 0;
     if (want_C) {
-        static std::vector<double> glx, glw;
-        if (glx.empty()) gauss_legendre(NGL, glx, glw);
-        KRY_CU(cudaMemcpyAsync(base + l.oGL, glx.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
-        KRY_CU(cudaMemcpyAsync(base + l.oGL + sizeof(double) * NGL, glw.data(), sizeof(double) * NGL,
-                               cudaMemcpyHostToDevice, s));
+        if (int rc = upload_gl(base + l.oGL, s)) return rc;
         ea.C = (double *)(base + l.oC);
         ea.glx = (const double *)(base + l.oGL);
         ea.glw = ea.glx + NGL;
@@ -362,7 +369,9 @@ Layout layout_b(const kry_ham_s *H, int dtype, int m, int grid, int n_times)
     l.oCtl = round_up(l.oPart + (size_t)grid * PSB * Kp * sizeof(double2), 256);
     l.oTimes = round_up(l.oCtl + sizeof(KryCtlB), 256);
     l.oP = round_up(l.oTimes + sizeof(double) * (size_t)n_times, 256);
-    l.bytes = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    l.oC = round_up(l.oP + sizeof(double) * (size_t)n_times * H->K, 256);
+    l.oGL = round_up(l.oC + sizeof(double) * (size_t)n_times * H->K, 256);
+    l.bytes = round_up(l.oGL + sizeof(double) * 2 * NGL, 256);
     return l;
 }
 
@@ -434,7 +443,7 @@ int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m,
 template <class V>
 int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool general,
               const double *times, int n_times, int m, double tol, void *d_psi_out, double *P_out,
-              kry_stats *st, cudaStream_t s)
+              kry_stats *st, cudaStream_t s, const uint64_t *states = nullptr, double *C_out = nullptr)
 {
     const DevBasis &b = H->b->dev;
     const int K = H->K, Kp = padded_k(K);
@@ -474,15 +483,22 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     ea.ldW = l.ldW;
     ea.c64 = dtype == KRY_C64;
     ea.K = K;
+    const int want_C = C_out ? 1 : 0;
+    if (want_C) {
+        if (int rc = upload_gl(base + l.oGL, s)) return rc;
+        ea.C = (double *)(base + l.oC);
+        ea.glx = (const double *)(base + l.oGL);
+        ea.glw = ea.glx + NGL;
+    }
     const int gkey = 2 + (int)general;   // distinguishes batched graphs from single ones
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != gkey ||
-                     H->g_grid != grid || H->g_gridB != gridB || H->g_ws != H->ws ||
+                     H->g_grid != grid || H->g_gridB != gridB || H->g_ws != H->ws || H->g_C != want_C ||
                      H->g_G != (const void *)(base + l.oP) || (int)H->prof_ev.empty() == H->prof_on))
         drop_graph(H);
     if (!H->gexec) {
         if (int rc = capture_step_b<V>(H, a, ea, m, grid, gridB, (int)general)) return rc;
         H->g_dtype = dtype; H->g_m = m; H->g_general = gkey; H->g_grid = grid; H->g_gridB = gridB;
-        H->g_ws = H->ws; H->g_G = base + l.oP;
+        H->g_ws = H->ws; H->g_G = base + l.oP; H->g_C = want_C;
     }
     cudaEvent_t ev0, ev1;
     KRY_CU(cudaEventCreate(&ev0));
@@ -504,16 +520,19 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     hd.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
     for (int k = 0; k < K; ++k) c->m_eff[k] = m;
     const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)K;
-    uint32_t r0 = 0;
     if (general) {
         hd.r0 = -1;
     } else {
-        uint64_t r = 0;
-        int j = 0;
-        for (int p = 0; p < b.L; ++p)
-            if ((state >> p) & 1ull) r += binom_host(p, ++j);
-        r0 = (uint32_t)r;
-        hd.r0 = (int)r;
+        // one basis state for every realisation, or one per realisation (states[k])
+        for (int k = 0; k < K; ++k) {
+            const uint64_t sk = states ? states[k] : state;
+            uint64_t r = 0;
+            int j = 0;
+            for (int p = 0; p < b.L; ++p)
+                if ((sk >> p) & 1ull) r += binom_host(p, ++j);
+            c->r0k[k] = (int)r;
+        }
+        hd.r0 = c->r0k[0];
         for (int k = 0; k < K; ++k) {
             c->beta0[k] = 1.0;
             c->sigma[0][k] = 1.0;
@@ -531,7 +550,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         if (int rc = launch_reduce_b(a.ctl, a.part, gridB, K, Kp, 5, 0, 1, 0, s)) return rc;
     } else {
         KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
-        if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, r0, s)) return rc;
+        if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, a.ctl, s)) return rc;
     }
     KryHdrB *hp = (KryHdrB *)H->h_poll;
     long long launched = 0;
@@ -573,6 +592,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         return hp->err;
     }
     KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * K, cudaMemcpyDeviceToHost, s));
+    if (want_C) KRY_CU(cudaMemcpyAsync(C_out, ea.C, sizeof(double) * n_times * K, cudaMemcpyDeviceToHost, s));
     if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
     std::vector<double> orth(K);
     KRY_CU(cudaMemcpyAsync(orth.data(), a.ctl->orth, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
@@ -701,27 +721,61 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
 // Temporal autocorrelation (Sec. 4): C(t) = (1/t) int_0^t P(t') dt' at the output times,
 // from the same evolution as P (the small exponential integrates P over each step of the
 // dense output by Gauss-Legendre quadrature).  Single realisation (K = 1).
+namespace {
+
+// Basis-state initial vectors with an optional temporal autocorrelation: states[k] (or the one
+// state) for realisation k; the single path for K = 1, the batched path otherwise.
+int evolve_states(kry_ham H, int dtype, const uint64_t *states, const double *times, int n_times, int m,
+                  double tol, double *P_out, double *C_out, kry_stats *stats, void *stream, const char *who)
+{
+    if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
+    if (!states) { set_error("%s: no initial states", who); return KRY_EINVAL; }
+    const int L = H->b->L;
+    for (int k = 0; k < H->K; ++k) {
+        if ((L < 64 && (states[k] >> L) != 0ull) || __builtin_popcountll(states[k]) != H->b->N) {
+            set_error("%s: state of realisation %d is not in the (L=%d, N=%d) sector", who, k, L, H->b->N);
+            return KRY_EINVAL;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (H->K > 1)
+        return dtype == KRY_C64
+                   ? evolve_bt<float2>(H, dtype, nullptr, 0, false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                                       states, C_out)
+                   : evolve_bt<double2>(H, dtype, nullptr, 0, false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                                        states, C_out);
+    EvOpts opt;
+    opt.C_out = C_out;
+    return dtype == KRY_C64
+               ? evolve_t<float2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats,
+                                  s, &opt)
+               : evolve_t<double2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats,
+                                   s, &opt);
+}
+
+}  // namespace
+
 extern "C" int kry_autocorrelation(kry_ham H, int dtype, uint64_t psi0_state, const double *times, int n_times,
                                    int m, double tol, double *C_out, double *P_out, kry_stats *stats,
                                    void *stream)
 {
     if (!C_out) { set_error("kry_autocorrelation: C_out is NULL"); return KRY_EINVAL; }
-    if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
-    if (H->K != 1) { set_error("kry_autocorrelation: needs a single realisation (K = 1)"); return KRY_EINVAL; }
-    const int L = H->b->L;
-    if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
-        set_error("kry_autocorrelation: state is not in the (L=%d, N=%d) sector", L, H->b->N);
-        return KRY_EINVAL;
-    }
-    EvOpts opt;
-    opt.C_out = C_out;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (dtype == KRY_C64)
-        return evolve_t<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s,
-                                &opt);
-    return evolve_t<double2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s,
-                             &opt);
+    if (!H) { set_error("kry_autocorrelation: H is NULL"); return KRY_EINVAL; }
+    std::vector<uint64_t> st((size_t)std::max(H->K, 1), psi0_state);
+    return evolve_states(H, dtype, st.data(), times, n_times, m, tol, P_out, C_out, stats, stream,
+                         "kry_autocorrelation");
 }
+
+// Ensembles of basis-state initial vectors (Sec. 2 disorder layers; Sec. 4): realisation k
+// starts from psi0_states[k]; P and, when C_out is given, C for every realisation.
+extern "C" int kry_return_probability_states(kry_ham H, int dtype, const uint64_t *psi0_states,
+                                             const double *times, int n_times, int m, double tol, double *P_out,
+                                             double *C_out, kry_stats *stats, void *stream)
+{
+    return evolve_states(H, dtype, psi0_states, times, n_times, m, tol, P_out, C_out, stats, stream,
+                         "kry_return_probability_states");
+}
+
 
 // ---------------------------------------------------------------- adjoint gradient
 //

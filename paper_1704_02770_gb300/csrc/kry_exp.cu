@@ -180,13 +180,13 @@ __device__ double2 step_readout(const ExpSmem &sm, double tp, double c, double r
 // (warp-collective: every lane passes the same s and gets the sum).  P is an entire
 // function of t' whose frequencies are bounded by the half-width r, and s r <= XMAX = 50,
 // so 64 nodes integrate it to rounding.
-__device__ double step_integral(const ExpSmem &sm, const ExpArgs &ea, double s, double c, double r, int K,
-                                double beta0, double *J)
+__device__ double step_integral(const ExpSmem &sm, const double *glx, const double *glw, double s, double c,
+                                double r, int K, double beta0, double *J)
 {
     double acc = 0.0;
     for (int q = threadIdx.x; q < NGL; q += 32) {
-        const double2 A = step_readout(sm, 0.5 * s * (1.0 + ea.glx[q]), c, r, K, beta0, J);
-        acc += ea.glw[q] * (A.x * A.x + A.y * A.y);
+        const double2 A = step_readout(sm, 0.5 * s * (1.0 + glx[q]), c, r, K, beta0, J);
+        acc += glw[q] * (A.x * A.x + A.y * A.y);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -342,11 +342,11 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
         for (int o = ctl->next_out; o < next; ++o) {
             const double to = ea.times[o];
             const double s = fmax(to - t_now, 0.0);
-            const double I = step_integral(sm, ea, s, c, r, K, beta0, myJ);
+            const double I = step_integral(sm, ea.glx, ea.glw, s, c, r, K, beta0, myJ);
             if (lane == 0) ea.C[o] = to > 0.0 ? (pint + I) / to : 1.0;
         }
         if (!last) {
-            const double I = step_integral(sm, ea, tau, c, r, K, beta0, myJ);
+            const double I = step_integral(sm, ea.glx, ea.glw, tau, c, r, K, beta0, myJ);
             if (lane == 0) ctl->pint = pint + I;
         }
         __syncwarp();
@@ -412,7 +412,7 @@ __device__ void load_tridiag_b(ExpSmem &sm, const KryCtlB *ctl, int k, int me, c
         sm.be[lane] = ctl->beta[lane][k];
         double2 g;
         if (ctl->hd.r0 >= 0) {
-            const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->hd.r0 * ea.K + k;
+            const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->r0k[k] * ea.K + k;
             double2 w;
             if (ea.c64) { float2 f = ((const float2 *)ea.W)[idx]; w = make_double2(f.x, f.y); }
             else w = ((const double2 *)ea.W)[idx];
@@ -554,25 +554,27 @@ __global__ void __launch_bounds__(32) k_exp_apply_b(ExpArgsB ea)
         const unsigned mk = __ballot_sync(0xffffffffu, in);
         const int cnt = __popc(mk & ~(mk + 1u));
         if (lane < cnt) {
-            bessel_seq(tp * r, Kc, myJ);
-            double re = 0.0, im = 0.0;
-            for (int kk = 0; kk <= Kc; ++kk) {
-                const double t = myJ[kk] * (kk == 0 ? 1.0 : 2.0);
-                const double2 G = sm.gk[kk];
-                switch (kk & 3) {
-                case 0: re += t * G.x; im += t * G.y; break;
-                case 1: re += t * G.y; im -= t * G.x; break;
-                case 2: re -= t * G.x; im -= t * G.y; break;
-                default: re -= t * G.y; im += t * G.x; break;
-                }
-            }
-            double sn, cs;
-            sincos(tp * c, &sn, &cs);
-            const double2 A = cmul(make_double2(cs, -sn), make_double2(re * beta0, im * beta0));
+            const double2 A = step_readout(sm, tp, c, r, Kc, beta0, myJ);
             ea.P[(size_t)o * ea.K + k] = A.x * A.x + A.y * A.y;
         }
         next += cnt;
         if (cnt < 32) break;
+    }
+    if (ea.C) {
+        // temporal autocorrelation of realisation k (Sec. 4), as in the single path
+        __syncwarp();
+        const double pint = ctl->pint[k];
+        for (int o = H.next_out; o < next; ++o) {
+            const double to = ea.times[o];
+            const double s = fmax(to - t_now, 0.0);
+            const double I = step_integral(sm, ea.glx, ea.glw, s, c, r, Kc, beta0, myJ);
+            if (lane == 0) ea.C[(size_t)o * ea.K + k] = to > 0.0 ? (pint + I) / to : 1.0;
+        }
+        if (!last) {
+            const double I = step_integral(sm, ea.glx, ea.glw, tau, c, r, Kc, beta0, myJ);
+            if (lane == 0) ctl->pint[k] = pint + I;
+        }
+        __syncwarp();
     }
     if (k == 0 && lane == 0) {
         H.next_out_new = next;

@@ -113,6 +113,8 @@ struct KryCtlB {
     double wnorm2[KBMAX];   // ||w||^2 of pass B, kept for pass C1
     double2 wg[KBMAX];      // <psi0, w> of pass B
     int dots[KBMAX];        // this realisation takes the dots of w (pass C1)
+    int r0k[KBMAX];         // basis index of each realisation's initial state (hd.r0 >= 0)
+    double pint[KBMAX];     // int_0^t_now P_k(t') dt' (temporal autocorrelation)
 };
 
 template <class V>
@@ -136,6 +138,8 @@ struct ExpArgsB {
     const void *W;
     size_t ldW;
     int c64, K;
+    double *C;       // nullable: temporal autocorrelation [n_times][K]
+    const double *glx, *glw;   // Gauss-Legendre nodes and weights on [-1, 1] (with C)
 };
 
 template <class V> int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s);
@@ -145,7 +149,7 @@ int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, 
 template <class V> int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB);
 int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
                    int rl_smem, cudaStream_t s);
-int launch_set_basis_state_b(void *W0, int c64, int K, uint32_t r0, cudaStream_t s);
+int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s);
 int launch_exp_b(const ExpArgsB &a, cudaStream_t s);
 
 // Device control block of one evolution: Lanczos coefficients of the current Krylov

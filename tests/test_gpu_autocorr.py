@@ -74,19 +74,85 @@ def test_repeated_and_zero_times(kry):
     assert np.max(np.abs(C - Cd)) <= 1e-10
 
 
-def test_rejects_batched_and_bad_arguments(kry):
+def test_rejects_bad_arguments(kry):
     L = 10
     B = kry.Basis(L, 5)
     h = workloads.quasiperiodic_field(L, 1.0, 0.4)
-    HK = kry.Hamiltonian(B, 1.0, 1.0, [h, h])
-    with pytest.raises(kry.KryError) as e:
-        HK.autocorrelation(workloads.neel_state(L), [1.0])
-    assert e.value.code == kry.KRY_EINVAL
     H = kry.Hamiltonian(B, 1.0, 1.0, h)
     with pytest.raises(kry.KryError):
         H.autocorrelation(0b111, [1.0])
     with pytest.raises(kry.KryError):
         H.autocorrelation(workloads.neel_state(L), [2.0, 1.0])
+    HK = kry.Hamiltonian(B, 1.0, 1.0, [h, h, h])
+    good = workloads.random_basis_states(L, 5, 7, 3)
+    with pytest.raises(ValueError):
+        HK.return_probability_states(good[:2], [1.0])
+    with pytest.raises(kry.KryError) as e:
+        HK.return_probability_states([good[0], 0b1111, good[2]], [1.0])
+    assert e.value.code == kry.KRY_EINVAL and "realisation 1" in str(e.value)
+
+
+def _ensemble_case(L, K, seed):
+    N = L // 2
+    hs = [workloads.quasiperiodic_field(L, 1.5, p) for p in workloads.phases(seed, K)]
+    states = workloads.random_basis_states(L, N, seed + 100, K)
+    return N, hs, states
+
+
+@pytest.mark.parametrize("dtype,tol,bar", [("c128", 1e-10, 1e-10), ("c64", 1e-7, 1e-5)])
+def test_random_state_ensemble_vs_spectral(kry, dtype, tol, bar):
+    """K = 6 realisations, each with its own phase and its own random basis state (batched
+    path): P and C of every realisation against the dense spectral oracle."""
+    L, K = 12, 6
+    N, hs, states = _ensemble_case(L, K, 21)
+    times = [0.0] + list(workloads.log_times(30, 0.1, 100.0))
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs)
+    P, C, _ = H.return_probability_states(states, times, tol=tol, dtype=dtype, autocorrelation=True)
+    P2, _ = H.return_probability_states(states, times, tol=tol, dtype=dtype)
+    assert np.array_equal(P, P2)   # computing C changes nothing in P
+    worst_c = worst_p = 0.0
+    for k in range(K):
+        Cd, Pd = _dense_C(L, N, 1.0, 1.0, hs[k], True, states[k], times)
+        worst_c = max(worst_c, float(np.max(np.abs(C[:, k] - Cd))))
+        worst_p = max(worst_p, float(np.max(np.abs(P[:, k] - Pd))))
+    print(f"[parity] ensemble L{L} K{K} {dtype}: max|dC| = {worst_c:.3e}, max|dP| = {worst_p:.3e}")
+    assert np.all(C[0] == 1.0) and np.all(P[0] == 1.0)
+    assert worst_c <= bar and worst_p <= bar
+
+
+def test_batched_autocorrelation_common_state(kry):
+    L, K = 14, 4
+    N, hs, _ = _ensemble_case(L, K, 22)
+    st = workloads.neel_state(L)
+    times = workloads.log_times(20, 0.1, 50.0)
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs)
+    C, P, _ = H.autocorrelation(st, times)
+    assert C.shape == (len(times), K)
+    for k in range(K):
+        Cd, _ = _dense_C(L, N, 1.0, 1.0, hs[k], True, st, times)
+        assert np.max(np.abs(C[:, k] - Cd)) <= 1e-10
+    Pr, _ = H.return_probability(st, times)
+    assert np.array_equal(P, Pr)
+
+
+def test_ensemble_full_size_L22(kry):
+    """L=22 (D = 705,432), K = 16 random basis states: per-realisation C against Simpson of the
+    call's own P on a grid of step 1/200 to t = 1, and 0 <= C <= 1, C(0) = 1."""
+    L, K = 22, 16
+    N, hs, states = _ensemble_case(L, K, 23)
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs)
+    grid = np.linspace(0.0, 1.0, 201)
+    P, C, st = H.return_probability_states(states, grid, tol=1e-10, autocorrelation=True)
+    hstep = grid[1] - grid[0]
+    w = np.ones(201)
+    w[1:-1:2] = 4.0
+    w[2:-1:2] = 2.0
+    simpson = hstep / 3.0 * (w @ P)
+    err = float(np.max(np.abs(C[-1] - simpson)))
+    print(f"[parity] ensemble L22 K16: max|C(1) - Simpson| = {err:.3e}")
+    assert err <= 2e-7
+    assert np.all(C[0] == 1.0) and np.all((C >= -1e-12) & (C <= 1.0 + 1e-12))
+    assert st["n_krylov_steps"] > 0
 
 
 @pytest.mark.parametrize("dtype,bar", [("c128", 2e-7), ("c64", 2e-5)])

@@ -47,6 +47,23 @@ def quasiperiodic_field(L: int, h: float, phi: float, q: float = GOLDEN_Q) -> li
     return [h * math.cos(2.0 * math.pi * q * i + phi) for i in range(1, L + 1)]
 
 
+def random_basis_states(L: int, N: int, seed: int, k: int) -> list[int]:
+    """k random product states of the (L, N) sector, each uniform over the C(L, N) site sets:
+    N sites drawn without replacement by a partial Fisher-Yates shuffle of 1..L, with
+    SplitMix64 draws (N per realisation) mapped to indices by floor(u * remaining)."""
+    u = uniform53(seed, k * N)
+    out = []
+    for r in range(k):
+        sites = list(range(L))
+        s = 0
+        for i in range(N):
+            j = i + min(int(u[r * N + i] * (L - i)), L - i - 1)
+            sites[i], sites[j] = sites[j], sites[i]
+            s |= 1 << sites[i]
+        out.append(s)
+    return out
+
+
 def neel_state(L: int) -> int:
     """Neel product state (...010101) of Sec. 4: sites 1, 3, 5, ... occupied (bits 0, 2, 4, ...)."""
     s = 0
