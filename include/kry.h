@@ -67,11 +67,18 @@ typedef struct kry_stats {
 } kry_stats;
 
 /* ---------------------------------------------------------------- basis (Sec. 2, Alg. 2)
- * Create the sector basis of L sites and n_up particles: 1 <= L <= 32, 0 <= n_up <= L.
- * No basis list is stored; rank and unrank tables of about 2^(L/2+2) bytes live on the
- * current device.  Returns KRY_EINVAL for bad sizes, KRY_ENOMEM/KRY_ECUDA on device
+ * Create the sector basis of L sites and n_up particles: 1 <= L <= 64, 0 <= n_up <= L.
+ * For L <= 32 no basis list is stored; rank and unrank tables of about 2^(L/2+2) bytes live
+ * on the current device.  For L > 32 the call returns the sorted-list form of
+ * kry_basis_create_list.  Returns KRY_EINVAL for bad sizes, KRY_ENOMEM/KRY_ECUDA on device
  * failure. */
 int kry_basis_create(int L, int n_up, kry_basis *out);
+/* Sorted-list form of the basis (the sorted integer list of Alg. 2, built on the device;
+ * 8 bytes per state) for 1 <= L <= 64 with D = C(L, n_up) <= 2^31 - 1 (KRY_EINVAL above).
+ * Ranks are combinadic numbers, rank(s) = sum_j C(p_j, j) over the occupied sites
+ * p_1 < ... < p_N, so lookups need no search.  Every call below accepts either form, except
+ * kry_grad, which needs L <= 32 and the split tables of kry_basis_create. */
+int kry_basis_create_list(int L, int n_up, kry_basis *out);
 int kry_basis_destroy(kry_basis b);
 /* Sector dimension D = L!/(N!(L-N)!) (Sec. 2); -1 for a NULL handle. */
 int64_t kry_basis_dim(kry_basis b);

@@ -36,6 +36,7 @@ class Stats(ctypes.Structure):
 
 SIGNATURES = {
     "kry_basis_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
+    "kry_basis_create_list": (_i, [_i, _i, ctypes.POINTER(_vp)]),
     "kry_basis_destroy": (_i, [_vp]),
     "kry_basis_dim": (_i64, [_vp]),
     "kry_basis_rank": (_i, [_vp, _vp, _vp, _i64, _vp]),
@@ -123,12 +124,15 @@ def _host_doubles(x):
 
 
 class Basis:
-    """Sector of L sites with n_up particles (Sec. 2); rank/unrank without a stored list."""
+    """Sector of L sites with n_up particles (Sec. 2): split rank tables for L <= 32, the
+    sorted list of Alg. 2 with combinadic ranks for L > 32 or when `list` is set."""
 
-    def __init__(self, L: int, n_up: int):
+    def __init__(self, L: int, n_up: int, list: bool = False):
         lib = load()
         h = _vp()
-        _check(lib.kry_basis_create(L, n_up, ctypes.byref(h)))
+        create = lib.kry_basis_create_list if list else lib.kry_basis_create
+        _check(create(L, n_up, ctypes.byref(h)))
+        self.list = bool(list) or L > 32
         self._h, self.L, self.n_up = h, L, n_up
         self.dim = int(lib.kry_basis_dim(h))
 

@@ -3,6 +3,7 @@
 // the Hamiltonian handle (Eq. 1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -96,12 +97,73 @@ using namespace kry;
 
 extern "C" const char *kry_last_error(void) { return g_err.c_str(); }
 
+// C(n, k) saturated at 2^63 (exact below it)
+static uint64_t binom_sat(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 r = 1;
+    for (int i = 1; i <= k; ++i) {
+        r = r * (unsigned)(n - k + i) / (unsigned)i;
+        if (r >= ((unsigned __int128)1 << 63)) return 1ull << 63;
+    }
+    return (uint64_t)r;
+}
+
+// Sorted-list basis of Alg. 2 (states on the device, combinadic ranks): 1 <= L <= 64.
+extern "C" int kry_basis_create_list(int L, int n_up, kry_basis *out)
+{
+    if (!out) { set_error("kry_basis_create_list: out is NULL"); return KRY_EINVAL; }
+    *out = nullptr;
+    if (L < 1 || L > 64 || n_up < 0 || n_up > L) {
+        set_error("kry_basis_create_list: need 1 <= L <= 64 and 0 <= n_up <= L (got L=%d, n_up=%d)", L, n_up);
+        return KRY_EINVAL;
+    }
+    const uint64_t D = binom_sat(L, n_up);
+    if (D > 0x7FFFFFFFull) {
+        set_error("kry_basis_create_list: sector dimension C(%d, %d) exceeds 2^31 - 1", L, n_up);
+        return KRY_EINVAL;
+    }
+    const int N1 = n_up + 1;
+    std::vector<uint32_t> cb((size_t)L * N1);
+    for (int p = 0; p < L; ++p)
+        for (int k = 0; k <= n_up; ++k) cb[(size_t)p * N1 + k] = (uint32_t)std::min<uint64_t>(binom_sat(p, k), 0xFFFFFFFFull);
+    const size_t o_st = 0, o_cb = (8 * (size_t)D + 255) & ~(size_t)255;
+    const size_t o_er = (o_cb + sizeof(uint32_t) * cb.size() + 15) & ~(size_t)15, bytes = o_er + 16;
+    kry_basis b = new (std::nothrow) kry_basis_s();
+    if (!b) { set_error("kry_basis_create_list: host allocation failed"); return KRY_ENOMEM; }
+    b->L = L; b->N = n_up; b->Llo = 0; b->Lhi = 0; b->D = (int64_t)D;
+    cudaGetDevice(&b->device);
+    cudaError_t e = cudaMalloc(&b->d_tab, bytes);
+    if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(basis list)"); }
+    char *base = (char *)b->d_tab;
+    DevBasis &d = b->dev;
+    d = DevBasis{};
+    d.list = 1;
+    d.states = (const uint64_t *)(base + o_st);
+    d.cbin = (const uint32_t *)(base + o_cb);
+    d.err = (int *)(base + o_er);
+    d.L = L; d.N = n_up; d.Llo = 0; d.Lhi = 0; d.D = (uint32_t)D;
+    e = cudaMemcpy(base + o_cb, cb.data(), sizeof(uint32_t) * cb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(base + o_er, 0, 16);
+    int rc = (e == cudaSuccess) ? list_build(d, 0) : KRY_OK;
+    if (e == cudaSuccess && rc == KRY_OK) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess || rc != KRY_OK) {
+        cudaFree(b->d_tab);
+        delete b;
+        return e != cudaSuccess ? cuda_fail(e, "basis list build") : rc;
+    }
+    *out = b;
+    return KRY_OK;
+}
+
 extern "C" int kry_basis_create(int L, int n_up, kry_basis *out)
 {
     if (!out) { set_error("kry_basis_create: out is NULL"); return KRY_EINVAL; }
     *out = nullptr;
-    if (L < 1 || L > 32 || n_up < 0 || n_up > L) {
-        set_error("kry_basis_create: need 1 <= L <= 32 and 0 <= n_up <= L (got L=%d, n_up=%d)",
+    if (L > 32 && L <= 64) return kry_basis_create_list(L, n_up, out);
+    if (L < 1 || L > 64 || n_up < 0 || n_up > L) {
+        set_error("kry_basis_create: need 1 <= L <= 64 and 0 <= n_up <= L (got L=%d, n_up=%d)",
                   L, n_up);
         return KRY_EINVAL;
     }
@@ -226,8 +288,15 @@ static int rank_common(kry_basis b, int64_t n, const void *in, void *out, void *
     cudaStream_t s = (cudaStream_t)stream;
     KRY_CU(cudaMemsetAsync(b->dev.err, 0, sizeof(int), s));
     int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-    if (unrank) k_unrank<<<grid, 256, 0, s>>>(b->dev, (const uint32_t *)in, (uint64_t *)out, n);
-    else k_rank<<<grid, 256, 0, s>>>(b->dev, (const uint64_t *)in, (uint32_t *)out, n);
+    if (b->dev.list) {
+        const int rc = unrank ? launch_list_unrank(b->dev, (const uint32_t *)in, (uint64_t *)out, n, s)
+                              : launch_list_rank(b->dev, (const uint64_t *)in, (uint32_t *)out, n, s);
+        if (rc) return rc;
+    } else if (unrank) {
+        k_unrank<<<grid, 256, 0, s>>>(b->dev, (const uint32_t *)in, (uint64_t *)out, n);
+    } else {
+        k_rank<<<grid, 256, 0, s>>>(b->dev, (const uint64_t *)in, (uint32_t *)out, n);
+    }
     KRY_CU(cudaGetLastError());
     int flag = 0;
     KRY_CU(cudaMemcpyAsync(&flag, b->dev.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -254,6 +323,55 @@ extern "C" int kry_basis_unrank(kry_basis b, const uint32_t *d_ranks, uint64_t *
 
 // ---------------------------------------------------------------- Hamiltonian handle
 
+// Sorted-list basis: field energy by bytes of the state, realisation fastest,
+//   sum_i h_{k,i} (n_i - 1/2) = sum_c eh8[(c * 256 + byte_c) * K + k]   (-sum_i h_{k,i}/2 in c = 0).
+static void fill_dev_ham(DevHam &d, double J, double Delta, int L, int K, int boundary)
+{
+    d.cz = 0.25 * J * Delta;
+    d.halfJ = 0.5 * J;
+    d.pbc = (boundary == KRY_PBC && L >= 3) ? 1 : 0;
+    d.nbonds = d.pbc ? L : (L - 1);
+    d.K = K;
+}
+
+static int ham_set_list(kry_basis b, double J, double Delta, const double *h, int K, int boundary, kry_ham *out)
+{
+    const int L = b->L, nc = (L + 7) / 8;
+    const size_t n8 = (size_t)nc * 256 * K;
+    std::vector<double> eh(n8);
+    std::vector<float> ehf(n8);
+    for (int k = 0; k < K; ++k) {
+        const double *hk = h + (size_t)k * L;
+        double hsum = 0.0;
+        for (int i = 0; i < L; ++i) hsum += hk[i];
+        for (int c = 0; c < nc; ++c)
+            for (int v = 0; v < 256; ++v) {
+                double e = (c == 0) ? -0.5 * hsum : 0.0;
+                for (int q = 0; q < 8 && 8 * c + q < L; ++q) if ((v >> q) & 1) e += hk[8 * c + q];
+                eh[((size_t)c * 256 + v) * K + k] = e;
+            }
+    }
+    for (size_t i = 0; i < n8; ++i) ehf[i] = (float)eh[i];
+    kry_ham H = new (std::nothrow) kry_ham_s();
+    if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
+    cudaError_t e = cudaMalloc(&H->d_eh, 12 * n8);
+    if (e != cudaSuccess) { delete H; return cuda_fail(e, "cudaMalloc(field tables)"); }
+    char *base = (char *)H->d_eh;
+    e = cudaMemcpy(base, eh.data(), 8 * n8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 8 * n8, ehf.data(), 4 * n8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(H->d_eh); delete H; return cuda_fail(e, "field upload"); }
+    H->b = b; H->J = J; H->Delta = Delta; H->K = K; H->boundary = boundary;
+    H->h.assign(h, h + (size_t)K * L);
+    DevHam &d = H->dev;
+    d = DevHam{};
+    d.eh8_d = (const double *)base;
+    d.eh8_f = (const float *)(base + 8 * n8);
+    d.nchunk = nc;
+    fill_dev_ham(d, J, Delta, L, K, boundary);
+    *out = H;
+    return KRY_OK;
+}
+
 extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const double *h, int K,
                                    int boundary, kry_ham *out)
 {
@@ -271,6 +389,7 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
         set_error("kry_hamiltonian_set: K = %d realisations exceeds the maximum %d", K, KBMAX);
         return KRY_EINVAL;
     }
+    if (b->dev.list) return ham_set_list(b, J, Delta, h, K, boundary, out);
     const int Llo = b->Llo, Lhi = b->Lhi;
     const uint32_t nlo = 1u << Llo, nhi = 1u << Lhi;
     // field energy tables, realisation fastest:

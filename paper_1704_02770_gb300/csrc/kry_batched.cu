@@ -594,6 +594,12 @@ int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB)
 template <class V>
 int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
 {
+    if (a.b.list) {
+        if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
+        KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
+        KRY_CU(cudaGetLastError());
+        return KRY_OK;
+    }
     const size_t sH = hv_b_smem(a.b, a.rl_smem);
     const uint32_t ntiles = (a.b.D + TROWS - 1) / TROWS;
     KRY_KQ_SWITCH(a.Kp, {
@@ -645,6 +651,7 @@ int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, 
 int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
                    int rl_smem, cudaStream_t s)
 {
+    if (b.list) return launch_list_apply(b, h, c64, K, x, y, s);
     int Kp = 32;
     while (Kp < K) Kp *= 2;
     const size_t smem = sizeof(SmemHeadB) + (rl_smem ? (sizeof(uint16_t) << b.Llo) : 0);

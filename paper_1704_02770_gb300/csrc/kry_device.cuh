@@ -14,6 +14,7 @@ template <> struct VT<double2> {
     __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
     __device__ __forceinline__ static double ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_d + p); }
     __device__ __forceinline__ static double ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_d + p); }
+    __device__ __forceinline__ static double eh8(const DevHam &h, size_t p) { return __ldg(h.eh8_d + p); }
     __device__ __forceinline__ static double2 from(double2 c) { return c; }
 };
 template <> struct VT<float2> {
@@ -21,6 +22,7 @@ template <> struct VT<float2> {
     __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
     __device__ __forceinline__ static float ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_f + p); }
     __device__ __forceinline__ static float ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_f + p); }
+    __device__ __forceinline__ static float eh8(const DevHam &h, size_t p) { return __ldg(h.eh8_f + p); }
     __device__ __forceinline__ static float2 from(double2 c) { return make_float2((float)c.x, (float)c.y); }
 };
 

@@ -34,7 +34,7 @@ size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int rl_in_smem(const DevBasis &b) { return b.Llo <= 15 ? 1 : 0; }
+int rl_in_smem(const DevBasis &b) { return (!b.list && b.Llo <= 15) ? 1 : 0; }
 
 struct Layout {
     size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, oY, oC, oGL, bytes;
@@ -848,6 +848,7 @@ extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double 
         return KRY_EINVAL;
     }
     if (H->K != 1) { set_error("kry_grad: one realisation (K = 1) only"); return KRY_EINVAL; }
+    if (H->b->dev.list) { set_error("kry_grad: needs the split-table basis (L <= 32)"); return KRY_EINVAL; }
     const int L = H->b->L;
     if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
         set_error("kry_grad: state is not in the (L=%d, N=%d) sector", L, H->b->N);

@@ -570,6 +570,7 @@ static int sm_count()
 int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y, int rl_smem,
                  cudaStream_t s)
 {
+    if (b.list) return launch_list_apply(b, h, c64, 1, x, y, s);
     const size_t smem = apply_smem(b, rl_smem, c64);
     const uint32_t ntiles = (b.D + TILE - 1) / TILE;
     int grid = (int)std::min<uint32_t>(ntiles, (uint32_t)sm_count() * 8u);
@@ -602,6 +603,9 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
         return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
     };
     *gridH = fit(occH);
+    if (b.list) {
+        if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
+    }
     *gridB = fit(occB);
     return fit(occA);
 }
@@ -609,6 +613,7 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
 {
+    if (a.b.list) return launch_list_hv<V>(a, jj, grid, s);
     KRY_CU(launch_pdl(k_hv<V>, grid, NTHR, apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2)), s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;

@@ -69,6 +69,10 @@ struct DevBasis {
     int *err;               // device error flag of rank/unrank
     int L, N, Llo, Lhi;
     uint32_t D;
+    // sorted-list basis (L > 32, or on request): the split tables above are unused
+    int list;
+    const uint64_t *states;   // [D] sorted states
+    const uint32_t *cbin;     // C(p, k) at [p * (N + 1) + k], p < L, k <= N (saturated at 2^32 - 1)
 };
 
 // Hamiltonian parameters for the matrix-free H.v.  The field energy
@@ -82,6 +86,11 @@ struct DevHam {
     int nbonds;     // bonds of the chain (L-1 open, L on a ring with L >= 3)
     int pbc;        // ring bond (L-1, 0) present
     int K;          // realisations (field rows)
+    // sorted-list basis: field energy by bytes of the state,
+    //   sum_i h_{k,i} (n_i - 1/2) = sum_c eh8[(c * 256 + byte_c(s)) * K + k]
+    const double *eh8_d;
+    const float *eh8_f;
+    int nchunk;     // bytes of a state, ceil(L / 8)
 };
 
 // ---------------------------------------------------------------- batched realisations
@@ -228,6 +237,16 @@ struct ExpArgs {
 constexpr int NGL = 64;   // Gauss-Legendre nodes of the per-step integral of P
 
 size_t apply_smem(const DevBasis &b, int rl_smem, int c64);
+
+// sorted-list basis (kry_list.cu)
+int list_build(DevBasis &b, cudaStream_t s);
+int launch_list_rank(const DevBasis &b, const uint64_t *st, uint32_t *rk, int64_t n, cudaStream_t s);
+int launch_list_unrank(const DevBasis &b, const uint32_t *rk, uint64_t *st, int64_t n, cudaStream_t s);
+int launch_list_apply(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y, cudaStream_t s);
+template <class V> int launch_list_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_list_hv_b(const EvArgsB<V> &a, int jj, cudaStream_t s);
+template <class V> int list_hv_grid(const DevBasis &b, int *grid);
+size_t list_smem(const DevBasis &b);
 
 // kernel launchers (kry_hv.cu)
 int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y,

@@ -45,8 +45,11 @@ def test_argument_validation_without_gpu(lib):
     import paper_1704_02770_gb300 as k
     h = ctypes.c_void_p()
     assert lib.kry_basis_create(0, 0, ctypes.byref(h)) == k.KRY_EINVAL
-    assert b"1 <= L <= 32" in lib.kry_last_error()
-    assert lib.kry_basis_create(33, 3, ctypes.byref(h)) == k.KRY_EINVAL
+    assert b"1 <= L <= 64" in lib.kry_last_error()
+    assert lib.kry_basis_create(65, 3, ctypes.byref(h)) == k.KRY_EINVAL
+    assert lib.kry_basis_create_list(65, 3, ctypes.byref(h)) == k.KRY_EINVAL
+    assert lib.kry_basis_create_list(40, 20, ctypes.byref(h)) == k.KRY_EINVAL   # D > 2^31 - 1
+    assert b"exceeds" in lib.kry_last_error()
     assert lib.kry_basis_create(8, 9, ctypes.byref(h)) == k.KRY_EINVAL
     assert lib.kry_basis_dim(None) == -1
     assert lib.kry_hamiltonian_set(None, 1.0, 1.0, None, 1, 1, ctypes.byref(h)) == k.KRY_EINVAL

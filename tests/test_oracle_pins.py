@@ -224,3 +224,25 @@ def test_arnoldi_is_orthonormal_and_tridiagonal():
     T = Hb[:me, :me]
     assert np.max(np.abs(np.triu(T, 2))) < 1e-12
     assert np.max(np.abs(T - T.conj().T)) < 1e-12
+
+
+@pytest.mark.parametrize("pbc", [True, False])
+def test_single_particle_ring_L55(pbc):
+    """N = 1 on L = 55 (the Fibonacci ring of Sec. 2 and Sec. 4): the oracle's sector matrix is
+    the tight-binding chain written out by hand, hopping J/2 between neighbouring sites (and
+    across the ring bond with PBC), diagonal h_i - sum(h)/2 + (J Delta/4)(n_bonds - 2 n_anti)
+    with n_anti = 2 antiparallel bonds inside the chain (1 at an open end)."""
+    import workloads
+    L, J, Delta = 55, 1.3, 0.7
+    h = np.asarray(workloads.aubry_andre_field(L, 2.0, J, 0.4))
+    Hc = ob.CSR(L, 1, J, Delta, h, pbc).dense()
+    nb = L if pbc else L - 1
+    T = np.zeros((L, L))
+    for i in range(L):
+        nanti = 2 if (pbc or 0 < i < L - 1) else 1
+        T[i, i] = h[i] - 0.5 * h.sum() + 0.25 * J * Delta * (nb - 2 * nanti)
+    for i in range(L - 1):
+        T[i, i + 1] = T[i + 1, i] = 0.5 * J
+    if pbc:
+        T[0, L - 1] = T[L - 1, 0] = 0.5 * J
+    assert np.max(np.abs(Hc - T)) < 1e-12   # sums of 55 bond terms in another order

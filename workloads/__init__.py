@@ -64,6 +64,25 @@ def random_basis_states(L: int, N: int, seed: int, k: int) -> list[int]:
     return out
 
 
+def fibonacci_beta(L: int) -> float:
+    """beta = F_{n-1} / F_n for a ring of L = F_n sites (Sec. 2: a rational approximant of the
+    inverse golden ratio that closes the quasiperiodic cycle on the ring, e.g. 34/55)."""
+    a, b = 1, 1
+    while b < L:
+        a, b = b, a + b
+    if b != L:
+        raise ValueError(f"L = {L} is not a Fibonacci number")
+    return a / b
+
+
+def aubry_andre_field(L: int, lam: float, J: float, phi: float, beta: float | None = None) -> list[float]:
+    """On-site field of the Aubry-Andre chain (Sec. 4) at lambda = h / t, with the hopping
+    t = J / 2 of Eq. 1's XXZ form: h_i = (lambda J / 2) cos(2 pi beta i + phi); beta defaults
+    to the Fibonacci ratio of L."""
+    q = fibonacci_beta(L) if beta is None else beta
+    return quasiperiodic_field(L, 0.5 * lam * J, phi, q)
+
+
 def neel_state(L: int) -> int:
     """Neel product state (...010101) of Sec. 4: sites 1, 3, 5, ... occupied (bits 0, 2, 4, ...)."""
     s = 0
