@@ -76,8 +76,7 @@ int kry_basis_create(int L, int n_up, kry_basis *out);
 /* Sorted-list form of the basis (the sorted integer list of Alg. 2, built on the device;
  * 8 bytes per state) for 1 <= L <= 64 with D = C(L, n_up) <= 2^31 - 1 (KRY_EINVAL above).
  * Ranks are combinadic numbers, rank(s) = sum_j C(p_j, j) over the occupied sites
- * p_1 < ... < p_N, so lookups need no search.  Every call below accepts either form, except
- * kry_grad, which needs L <= 32 and the split tables of kry_basis_create. */
+ * p_1 < ... < p_N, so lookups need no search.  Every call below accepts either form. */
 int kry_basis_create_list(int L, int n_up, kry_basis *out);
 int kry_basis_destroy(kry_basis b);
 /* Sector dimension D = L!/(N!(L-N)!) (Sec. 2); -1 for a NULL handle. */

@@ -848,7 +848,6 @@ extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double 
         return KRY_EINVAL;
     }
     if (H->K != 1) { set_error("kry_grad: one realisation (K = 1) only"); return KRY_EINVAL; }
-    if (H->b->dev.list) { set_error("kry_grad: needs the split-table basis (L <= 32)"); return KRY_EINVAL; }
     const int L = H->b->L;
     if ((L < 64 && (psi0_state >> L) != 0ull) || __builtin_popcountll(psi0_state) != H->b->N) {
         set_error("kry_grad: state is not in the (L=%d, N=%d) sector", L, H->b->N);
@@ -894,12 +893,13 @@ extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double 
     KRY_CU(cudaMalloc(&blamA.p, vb));
     KRY_CU(cudaMalloc(&blamB.p, vb));
     KRY_CU(cudaMalloc(&bw.p, sizeof(double) * wq.size()));
-    KRY_CU(cudaMalloc(&bacc.p, sizeof(double2) * (MMAX + 2) + 64));
+    constexpr int NACC = 66;   // L <= 64 sites and Delta
+    KRY_CU(cudaMalloc(&bacc.p, sizeof(double2) * NACC + 64));
     const int ggrid = (int)std::min<size_t>((D + TILE - 1) / TILE, 152 * 2);
     KRY_CU(cudaMalloc(&bpart.p, sizeof(double2) * PSTRIDE * (size_t)ggrid));
     double2 *acc = (double2 *)bacc.p;
-    unsigned *counter = (unsigned *)(acc + MMAX + 2);
-    KRY_CU(cudaMemsetAsync(bacc.p, 0, sizeof(double2) * (MMAX + 2) + 64, s));
+    unsigned *counter = (unsigned *)(acc + NACC);
+    KRY_CU(cudaMemsetAsync(bacc.p, 0, sizeof(double2) * NACC + 64, s));
     KRY_CU(cudaMemcpyAsync(bw.p, wq.data(), sizeof(double) * wq.size(), cudaMemcpyHostToDevice, s));
     KRY_CU(cudaMemsetAsync(bpsi0.p, 0, vb, s));
     if (int rc = launch_set_basis_state(bpsi0.p, 0, (uint32_t)r0, s)) return rc;

@@ -481,29 +481,34 @@ __global__ void __launch_bounds__(NTHR) k_ckpt(const V *__restrict__ W0, V *__re
 __global__ void __launch_bounds__(NTHR) k_grad_acc(DevBasis b, DevHam hm, double J, const double2 *__restrict__ psi,
                                                    const double2 *__restrict__ lam, size_t ld,
                                                    const double *__restrict__ w, int nq, double2 *part,
-                                                   double2 *acc_out, unsigned *counter)
+                                                   double2 *acc_out, unsigned *counter, int site0)
 {
     __shared__ uint32_t koff_s[20], bsz_s[20];
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wtmp[NTHR / 32];
     __shared__ int flag;
     const int tid = threadIdx.x, L = b.L;
-    stage_tables(b, koff_s, bsz_s, nullptr, 0);
+    if (!b.list) stage_tables(b, koff_s, bsz_s, nullptr, 0);
     if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
     __syncthreads();
     double2 acc[MMAX + 1];
 #pragma unroll
     for (int i = 0; i <= MMAX; ++i) acc[i] = make_double2(0.0, 0.0);
     const uint32_t D = b.D, ntiles = (D + TILE - 1) / TILE;
-    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint64_t obc = (L >= 2) ? ((1ull << (L - 1)) - 1ull) : 0ull;
     const double czz = 0.25 * J;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t r = tile * TILE + tid;
         if (r >= D) continue;
-        uint32_t hi, off;
-        int klo;
-        tile_unrank(b, bsz_s, tile * TILE, tid, hi, off, klo);
-        const uint32_t s = (hi << b.Llo) | __ldg(b.lolist + koff_s[klo] + off);
+        uint64_t s;
+        if (b.list) {
+            s = __ldg(b.states + r);
+        } else {
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(b, bsz_s, tile * TILE, tid, hi, off, klo);
+            s = ((uint64_t)hi << b.Llo) | __ldg(b.lolist + koff_s[klo] + off);
+        }
         double2 S = make_double2(0.0, 0.0);
         for (int q = 0; q < nq; ++q) {
             const double2 l = __ldg(lam + (size_t)(nq - 1 - q) * ld + r), p = __ldg(psi + (size_t)q * ld + r);
@@ -513,27 +518,30 @@ __global__ void __launch_bounds__(NTHR) k_grad_acc(DevBasis b, DevHam hm, double
         }
 #pragma unroll
         for (int i = 0; i < MMAX; ++i) {
-            if (i < L) {
-                const double z = ((s >> i) & 1u) ? 0.5 : -0.5;
+            if (site0 + i < L) {
+                const double z = ((s >> (site0 + i)) & 1ull) ? 0.5 : -0.5;
                 acc[i].x += z * S.x;
                 acc[i].y += z * S.y;
             }
         }
-        const int nanti = __popc((s ^ (s >> 1)) & obc) + (hm.pbc ? (int)((s ^ (s >> (L - 1))) & 1u) : 0);
-        const double zz = czz * (double)(hm.nbonds - 2 * nanti);
-        acc[MMAX].x += zz * S.x;
-        acc[MMAX].y += zz * S.y;
+        if (site0 == 0) {
+            const int nanti = __popcll((long long)((s ^ (s >> 1)) & obc)) +
+                              (hm.pbc ? (int)((s ^ (s >> (L - 1))) & 1ull) : 0);
+            const double zz = czz * (double)(hm.nbonds - 2 * nanti);
+            acc[MMAX].x += zz * S.x;
+            acc[MMAX].y += zz * S.y;
+        }
     }
 #pragma unroll
     for (int i = 0; i <= MMAX; ++i) {
-        if (i < L || i == MMAX) cta_sum_into(acc[i], red, i, wtmp);
+        if (site0 + i < L || i == MMAX) cta_sum_into(acc[i], red, i, wtmp);
     }
     double2 *fin = red;
     if (!finish_partials(red, part, nullptr, fin, &flag, counter)) return;
-    if (tid < L) {
-        acc_out[tid].x += fin[tid].x;
-        acc_out[tid].y += fin[tid].y;
-    } else if (tid == L) {
+    if (tid < MMAX && site0 + tid < L) {
+        acc_out[site0 + tid].x += fin[tid].x;
+        acc_out[site0 + tid].y += fin[tid].y;
+    } else if (tid == MMAX && site0 == 0) {
         acc_out[L].x += fin[MMAX].x;
         acc_out[L].y += fin[MMAX].y;
     }
@@ -660,8 +668,10 @@ int launch_grad_acc(const DevBasis &b, const DevHam &h, double J, const double2 
                     size_t ld, const double *w, int nq, double2 *part, double2 *acc, unsigned *counter,
                     int grid, cudaStream_t s)
 {
-    k_grad_acc<<<grid, NTHR, 0, s>>>(b, h, J, psi, lam, ld, w, nq, part, acc, counter);
-    KRY_CU(cudaGetLastError());
+    for (int site0 = 0; site0 < b.L; site0 += MMAX) {   // 32 sites per launch (L > 32: two)
+        k_grad_acc<<<grid, NTHR, 0, s>>>(b, h, J, psi, lam, ld, w, nq, part, acc, counter, site0);
+        KRY_CU(cudaGetLastError());
+    }
     return KRY_OK;
 }
 

@@ -183,14 +183,34 @@ def test_random_state_ensemble_L55(kry):
         assert np.max(np.abs(C[:, k] - dense.autocorrelation_dense(Hd, psi0, times))) <= 1e-10
 
 
-def test_gradient_rejects_list_basis(kry):
-    H = kry.Hamiltonian(kry.Basis(12, 6, list=True), 1.0, 1.0, [0.1] * 12)
-    with pytest.raises(kry.KryError):
-        kry.load()
-        import ctypes
-        P = ctypes.c_double()
-        dh = (ctypes.c_double * 12)()
-        dd = ctypes.c_double()
-        rc = kry.load().kry_grad(H._h, ctypes.c_uint64(workloads.neel_state(12)), 1.0, 30, 1e-10, 8,
-                                 ctypes.byref(P), dh, ctypes.byref(dd), None, None)
-        kry._check(rc)
+@pytest.mark.parametrize("L,N,t", [(55, 1, 5.0), (40, 2, 3.0)])
+def test_grad_list_basis_vs_daleckii_krein(kry, L, N, t):
+    """kry_grad on the sorted-list basis (two blocks of 32 sites when L > 32) against the
+    oracle's Daleckii-Krein gradient of its dense CSR matrix.  dH/dh_i = Sz_i from the state
+    bits; dH/dDelta = H(Delta = 1) - H(Delta = 0) (H is linear in Delta)."""
+    from oracle import gradient
+    h = np.asarray(workloads.aubry_andre_field(L, 2.0, 1.0, 0.3) if L == 55
+                   else workloads.quasiperiodic_field(L, 1.0, 0.4))
+    st = (1 << 27) if N == 1 else ((1 << 3) | (1 << 21))
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, h)
+    P, gh, gd, _ = H.grad(st, t, tol=1e-11, ckpt_every=2)
+    Hc = ob.CSR(L, N, 1.0, 1.0, h, True)
+    states = Hc.basis
+    sz = [np.where((states >> np.uint64(i)) & np.uint64(1), 0.5, -0.5) for i in range(L)]
+    zz = np.diag(Hc.dense() - ob.CSR(L, N, 1.0, 0.0, h, True).dense())
+    psi0 = np.zeros(Hc.D, complex)
+    psi0[ob.lookup(states, st)] = 1.0
+    Pd, gdk = gradient.daleckii_krein(Hc.dense(), sz + [zz], psi0, t)
+    err = max(float(np.max(np.abs(np.asarray(gh) - np.asarray(gdk[:L])))), abs(gd - gdk[L]))
+    print(f"[parity] grad list basis L{L} N{N}: |dP| = {abs(P - Pd):.2e}, max|dgrad| = {err:.3e}")
+    assert abs(P - Pd) <= 1e-10 and err <= 1e-9
+
+
+def test_grad_list_equals_split_tables(kry):
+    c = workloads.config("L16_fp64")
+    out = []
+    for lst in (False, True):
+        H = kry.Hamiltonian(kry.Basis(16, 8, list=lst), 1.0, 1.0, c["h"][0])
+        P, gh, gd, _ = H.grad(c["state"], 2.0, tol=1e-11, ckpt_every=4)
+        out.append(np.r_[P, gh, gd])
+    assert np.max(np.abs(out[0] - out[1])) <= 1e-10
