@@ -141,7 +141,7 @@ def barrier(world):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kry_hv.cu", "kry_device.cuh", "kry_internal.cuh"):
+    for f in ("kry_hv.cu", "kry_batched.cu", "kry_device.cuh", "kry_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1704_02770_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -183,7 +183,7 @@ def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
     return per * D * krylov_steps
 
 
-def roofline(prof, form, D, c, L, N, clocks):
+def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
     """Roofline of the dominant kernel kind over a profiled timed region.
 
     complex128: every element costs FP64 arithmetic, and GB300's FP64 pipe (4 flop/clk/SM)
@@ -199,7 +199,9 @@ def roofline(prof, form, D, c, L, N, clocks):
     nl = max(prof[dom]["launches"], 1)
     hbm = {"achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
            "peak_source": "measured" if peaks else "fallback"}
-    tr = ncu_traffic(dom, prof[dom]["bytes"] / nl) if form == "c128" else ncu_traffic_c64(dom, prof[dom]["bytes"] / nl)
+    if traffic_key is None:
+        traffic_key = "" if form == "c128" else "c64_"
+    tr = ncu_traffic(traffic_key + dom, prof[dom]["bytes"] / nl)
     share = {k: prof[k]["ms"] / sum(prof[q]["ms"] for q in KIND_NAMES) for k in KIND_NAMES}
     if form == "c128":
         # Krylov steps that did work (replays after the last output time are no-ops):
@@ -224,11 +226,6 @@ def roofline(prof, form, D, c, L, N, clocks):
 TIMING_NOTE = ("per-kind CUDA-event times from a second timed region of the same evolutions with "
                "event nodes captured between the kernels of the step graph; value comes from the "
                "uninstrumented region")
-
-
-def ncu_traffic_c64(kind, algo_bytes_per_launch):
-    """As ncu_traffic, for the complex64 kernels (keys prefixed c64_)."""
-    return ncu_traffic("c64_" + kind, algo_bytes_per_launch)
 
 
 # ---------------------------------------------------------------- our arm
@@ -309,7 +306,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": Bb.dim * Hb.K * hvb / secb, "unit": "state-updates/s",
                               "ms_per_step": 1e3 * secb / args.steps, "workload": "L22_batched_h1.5 K=64 c64",
-                              "roofline": roofline(profb, "c64", Bb.dim * Hb.K, cb, cb["L"], cb["n_up"], clocks),
+                              "roofline": roofline(profb, "c64", Bb.dim * Hb.K, cb, cb["L"], cb["n_up"], clocks,
+                                                   traffic_key="b64_"),
                               "clocks": clocks}))
         return
     form = args.form if args.kernels_only else "c128"
@@ -363,7 +361,7 @@ def run_ours(args):
             "krylov_steps_per_step": stb["n_krylov_steps"],
             "speedup_vs_fp64": (ub / sb) / value,
             "disorder_avg_P_last": float(np.mean(Pb[-1])),
-            "roofline": roofline(profb, "c64", Bb.dim * Kb, cb, cb["L"], cb["n_up"], clocks)}
+            "roofline": roofline(profb, "c64", Bb.dim * Kb, cb, cb["L"], cb["n_up"], clocks, traffic_key="b64_")}
         out["gpu_launches"] += lb
         del Hb, Bb
     cfg["autotune"] = {k: {"grid": v["grid"], "probe_ms": v["candidates"]} for k, v in tune.items()}
