@@ -41,16 +41,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-widened", action="store_true",
+                    help="skip the temporal autocorrelation, random-state ensemble and L = 55 ring lines")
     ap.add_argument("--form", default="c128", choices=["c128", "c64", "c64b"],
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs)")
-    ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b"],
+    ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b", "c64l"],
                     help="one Krylov step (m = 30, one output time) of the workload, nothing else: "
                          "a short, fixed launch sequence for ncu captures")
     a = ap.parse_args()
     if a.kernels_only:
-        a.no_mixed = a.no_cpu_baseline = a.no_batched = True
+        a.no_mixed = a.no_cpu_baseline = a.no_batched = a.no_widened = True
     return a
 
 
@@ -363,6 +365,10 @@ def run_ours(args):
             "disorder_avg_P_last": float(np.mean(Pb[-1])),
             "roofline": roofline(profb, "c64", Bb.dim * Kb, cb, cb["L"], cb["n_up"], clocks, traffic_key="b64_")}
         out["gpu_launches"] += lb
+    if not args.no_widened:
+        out["widened"] = widened(args, kry, workloads, H, c, D, out, world)
+        out["gpu_launches"] += out["widened"].pop("_launches")
+    if not args.no_batched:
         del Hb, Bb
     cfg["autotune"] = {k: {"grid": v["grid"], "probe_ms": v["candidates"]} for k, v in tune.items()}
     out["config"] = cfg
@@ -403,6 +409,92 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def widened(args, kry, workloads, H, c, D, out, world):
+    """Throughput of the rows widened past the hot path, each from CUDA events around whole
+    calls of its public entry point (inputs resident, one warm-up call first):
+      autocorrelation   kry_autocorrelation (P and C(t)) on the L = 24 workload, complex64
+      ensemble          kry_return_probability_states: L = 22, K = 64 random basis states
+                        with their own phases, complex64, 40 log times in [0.1, 10]
+      list_basis        the L = 55 Fibonacci ring at N = 5 (D = 3,478,761, sorted-list basis,
+                        Aubry-Andre field at lambda = 2), complex128 and complex64"""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    launches = 0
+
+    def clock(fn, n_warm, n_steps):
+        nonlocal launches
+        for _ in range(n_warm):
+            fn()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hv = 0
+        res = None
+        e0.record(stream)
+        for _ in range(n_steps):
+            res = fn()
+            hv += res[-1]["n_hv"]
+            launches += res[-1]["n_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1) / 1e3, hv, res
+
+    w = {}
+    # temporal autocorrelation on the L = 24 workload (complex64)
+    sec, hv, (C, P, st) = clock(lambda: H.autocorrelation(c["state"], c["times"], m=c["m"], tol=1e-7,
+                                                          dtype="c64"), 1, args.steps)
+    u, s = aggregate(D * hv, sec, world)
+    ref = out.get("mixed", {}).get("value")
+    w["autocorrelation"] = {
+        "workload": "L24_mixed, complex64, P and C(t) at the 40 log times (tol 1e-7)",
+        "value": u / s, "unit": "state-updates/s", "ms_per_step": 1e3 * s / args.steps,
+        "time_vs_P_only": (ref / (u / s)) if ref else None,
+        "C_last": float(C[-1]), "gamma_fit_t10_100": kry.decay_exponent(c["times"], C, 10.0, 100.0)[0]}
+    # random-initial-state ensemble: L = 22, K = 64
+    cb = workloads.config("L22_batched_h1.5")
+    Kb = len(cb["h"])
+    Bb = kry.Basis(cb["L"], cb["n_up"])
+    Hb = kry.Hamiltonian(Bb, cb["J"], cb["Delta"], cb["h"], pbc=cb["pbc"])
+    states = workloads.random_basis_states(cb["L"], cb["n_up"], 6, Kb)
+    tb = workloads.log_times(40, 0.1, 10.0)
+    sec, hv, (Pb, Cb, st) = clock(lambda: Hb.return_probability_states(states, tb, m=cb["m"], tol=1e-7,
+                                                                        dtype="c64", autocorrelation=True), 1, 1)
+    u, s = aggregate(Bb.dim * Kb * hv, sec, world)
+    w["ensemble"] = {
+        "workload": f"L=22 N_up=11 D={Bb.dim} K={Kb}: random basis states (seed 6), phases of "
+                    "L22_batched_h1.5, 40 log times in [0.1,10], P and C, tol 1e-7",
+        "dtype": "c64 vectors [D][K], fp64 coefficients", "value": u / s,
+        "unit": "state-updates/s (D x K x H.v / s)", "ms_per_step": 1e3 * s, "steps": 1,
+        "ensemble_avg_C_last": float(np.mean(Cb[-1]))}
+    del Hb, Bb
+    # the L = 55 Fibonacci ring, N = 5, on the sorted-list basis
+    L5, N5 = 55, 5
+    h5 = workloads.aubry_andre_field(L5, 2.0, 1.0, workloads.phases(7)[0])
+    st5 = sum(1 << (11 * i) for i in range(N5))
+    B5 = kry.Basis(L5, N5)
+    H5 = kry.Hamiltonian(B5, 1.0, 1.0, h5)
+    lb = {"workload": f"L=55 ring, beta=34/55, N_up=5, D={B5.dim}, Aubry-Andre lambda=2 (phi seed 7), "
+                      "Delta=1, psi0 = sites 1,12,23,34,45, m=30, 40 log times in [0.1,100]",
+          "basis": "sorted list (Alg. 2), combinadic ranks"}
+    for dt, tl in (("c128", 1e-10), ("c64", 1e-7)):
+        H5.autotune(st5, 1.0, dtype=dt)
+        sec, hv, (P5, st) = clock(lambda: H5.return_probability(st5, c["times"], m=30, tol=tl, dtype=dt), 1, 1)
+        u, s = aggregate(B5.dim * hv, sec, world)
+        H5.profile(True)
+        H5.return_probability(st5, c["times"], m=30, tol=tl, dtype=dt)
+        pr = H5.profile_read()
+        H5.profile(False)
+        lb[dt] = {"value": u / s, "unit": "state-updates/s", "ms_per_step": 1e3 * s,
+                  "krylov_steps": st["n_krylov_steps"],
+                  "GBps_by_kind": {k: (v["bytes"] / (v["ms"] * 1e6) if v["ms"] else None) for k, v in pr.items()}}
+    w["list_basis"] = lb
+    del H5, B5
+    w["_launches"] = launches
+    return w
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -477,7 +569,7 @@ def run_ncu_case(args):
     warm-up, so that a kernel's launch index is known: per Lanczos index j the launches
     are k_hv, k_dots (pass A), k_lincomb (pass B), k_dots, k_lincomb (pass C, no-ops unless
     flagged), then the small exponential and the combine.  c64b: the batched K = 64
-    ensemble of L = 22 in complex64."""
+    ensemble of L = 22 in complex64.  c64l: the L = 55, N = 5 ring (sorted-list basis)."""
     import numpy as np
     import torch
 
@@ -486,6 +578,14 @@ def run_ncu_case(args):
 
     kry.load()
     torch.cuda.set_device(0)
+    if args.ncu_case == "c64l":   # the L = 55, N = 5 ring on the sorted-list basis
+        B = kry.Basis(55, 5)
+        H = kry.Hamiltonian(B, 1.0, 1.0, workloads.aubry_andre_field(55, 2.0, 1.0, workloads.phases(7)[0]))
+        P, st = H.return_probability(sum(1 << (11 * i) for i in range(5)), [0.5], m=30, tol=1e-7, dtype="c64")
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": "c64l", "workload": "L55 N5 ring", "krylov_steps": st["n_krylov_steps"],
+                          "hv": st["n_hv"], "P": float(np.asarray(P).ravel()[0])}))
+        return
     batched = args.ncu_case == "c64b"   # the K = 64 phase ensemble of L = 22
     c = workloads.config("L22_batched_h1.5" if batched else args.workload)
     B = kry.Basis(c["L"], c["n_up"])
