@@ -323,6 +323,16 @@ extern "C" int kry_basis_unrank(kry_basis b, const uint32_t *d_ranks, uint64_t *
 
 // ---------------------------------------------------------------- Hamiltonian handle
 
+// s_k = tr(H_k) / D, the mean diagonal of the sector: every bond is antiparallel in a fraction
+// 2N(L-N)/(L(L-1)) of the states and every site occupied in a fraction N/L.
+static double mean_diagonal(int L, int N, double J, double Delta, const double *hk, int nbonds)
+{
+    const double panti = (L >= 2) ? 2.0 * N * (double)(L - N) / ((double)L * (L - 1)) : 0.0;
+    double e = 0.25 * J * Delta * (nbonds - 2.0 * nbonds * panti);
+    for (int i = 0; i < L; ++i) e += hk[i] * ((double)N / L - 0.5);
+    return e;
+}
+
 // Sorted-list basis: field energy by bytes of the state, realisation fastest,
 //   sum_i h_{k,i} (n_i - 1/2) = sum_c eh8[(c * 256 + byte_c) * K + k]   (-sum_i h_{k,i}/2 in c = 0).
 static void fill_dev_ham(DevHam &d, double J, double Delta, int L, int K, int boundary)
@@ -354,20 +364,33 @@ static int ham_set_list(kry_basis b, double J, double Delta, const double *h, in
     for (size_t i = 0; i < n8; ++i) ehf[i] = (float)eh[i];
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
-    cudaError_t e = cudaMalloc(&H->d_eh, 12 * n8);
+    fill_dev_ham(H->dev, J, Delta, L, K, boundary);
+    // shifted copy for the Lanczos pass: s_k taken off the byte-0 entries
+    H->shift.resize(K);
+    std::vector<double> ehs(eh);
+    for (int k = 0; k < K; ++k) {
+        H->shift[k] = mean_diagonal(L, b->N, J, Delta, h + (size_t)k * L, H->dev.nbonds);
+        for (int v = 0; v < 256; ++v) ehs[(size_t)v * K + k] -= H->shift[k];
+    }
+    std::vector<float> ehsf(n8);
+    for (size_t i = 0; i < n8; ++i) ehsf[i] = (float)ehs[i];
+    cudaError_t e = cudaMalloc(&H->d_eh, 24 * n8);
     if (e != cudaSuccess) { delete H; return cuda_fail(e, "cudaMalloc(field tables)"); }
     char *base = (char *)H->d_eh;
     e = cudaMemcpy(base, eh.data(), 8 * n8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(base + 8 * n8, ehf.data(), 4 * n8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 12 * n8, ehs.data(), 8 * n8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + 20 * n8, ehsf.data(), 4 * n8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(H->d_eh); delete H; return cuda_fail(e, "field upload"); }
     H->b = b; H->J = J; H->Delta = Delta; H->K = K; H->boundary = boundary;
     H->h.assign(h, h + (size_t)K * L);
     DevHam &d = H->dev;
-    d = DevHam{};
     d.eh8_d = (const double *)base;
     d.eh8_f = (const float *)(base + 8 * n8);
     d.nchunk = nc;
-    fill_dev_ham(d, J, Delta, L, K, boundary);
+    H->dev_lz = d;
+    H->dev_lz.eh8_d = (const double *)(base + 12 * n8);
+    H->dev_lz.eh8_f = (const float *)(base + 20 * n8);
     *out = H;
     return KRY_OK;
 }
@@ -417,21 +440,31 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
             ehhi[(size_t)hi * K + k] = e;
         }
     }
-    std::vector<float> ehlo_f(ehlo.size()), ehhi_f(ehhi.size());
-    for (size_t p = 0; p < ehlo.size(); ++p) ehlo_f[p] = (float)ehlo[p];
-    for (size_t p = 0; p < ehhi.size(); ++p) ehhi_f[p] = (float)ehhi[p];
-    const size_t nl = (size_t)nlo * K, nh = (size_t)nhi * K;
-    size_t o_ld = 0, o_hd = o_ld + 8 * nl, o_lf = o_hd + 8 * nh;
-    size_t o_hf = o_lf + 4 * nl, bytes = o_hf + 4 * nh;
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
+    fill_dev_ham(H->dev, J, Delta, L, K, boundary);
+    // shifted copy of the upper-bit table for the Lanczos pass: s_k taken off every entry
+    H->shift.resize(K);
+    std::vector<double> ehhs(ehhi);
+    for (int k = 0; k < K; ++k) {
+        H->shift[k] = mean_diagonal(L, b->N, J, Delta, h + (size_t)k * L, H->dev.nbonds);
+        for (uint32_t hi = 0; hi < nhi; ++hi) ehhs[(size_t)hi * K + k] -= H->shift[k];
+    }
+    std::vector<float> ehlo_f(ehlo.size()), ehhi_f(ehhi.size()), ehhs_f(ehhs.size());
+    for (size_t p = 0; p < ehlo.size(); ++p) ehlo_f[p] = (float)ehlo[p];
+    for (size_t p = 0; p < ehhi.size(); ++p) { ehhi_f[p] = (float)ehhi[p]; ehhs_f[p] = (float)ehhs[p]; }
+    const size_t nl = (size_t)nlo * K, nh = (size_t)nhi * K;
+    size_t o_ld = 0, o_hd = o_ld + 8 * nl, o_lf = o_hd + 8 * nh;
+    size_t o_hf = o_lf + 4 * nl, o_sd = o_hf + 4 * nh, o_sf = o_sd + 8 * nh, bytes = o_sf + 4 * nh;
     cudaError_t e = cudaMalloc(&H->d_eh, bytes);
     if (e != cudaSuccess) { delete H; return cuda_fail(e, "cudaMalloc(field tables)"); }
     char *base = (char *)H->d_eh;
-    cudaMemcpy(base + o_ld, ehlo.data(), 8 * nl, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_hd, ehhi.data(), 8 * nh, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_lf, ehlo_f.data(), 4 * nl, cudaMemcpyHostToDevice);
-    e = cudaMemcpy(base + o_hf, ehhi_f.data(), 4 * nh, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(base + o_ld, ehlo.data(), 8 * nl, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_hd, ehhi.data(), 8 * nh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_lf, ehlo_f.data(), 4 * nl, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_hf, ehhi_f.data(), 4 * nh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_sd, ehhs.data(), 8 * nh, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + o_sf, ehhs_f.data(), 4 * nh, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(H->d_eh); delete H; return cuda_fail(e, "field upload"); }
     H->b = b; H->J = J; H->Delta = Delta; H->K = K; H->boundary = boundary;
     H->h.assign(h, h + (size_t)K * L);
@@ -440,11 +473,9 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
     d.ehhi_d = (const double *)(base + o_hd);
     d.ehlo_f = (const float *)(base + o_lf);
     d.ehhi_f = (const float *)(base + o_hf);
-    d.cz = 0.25 * J * Delta;
-    d.halfJ = 0.5 * J;
-    d.pbc = (boundary == KRY_PBC && L >= 3) ? 1 : 0;
-    d.nbonds = d.pbc ? L : (L - 1);
-    d.K = K;
+    H->dev_lz = d;
+    H->dev_lz.ehhi_d = (const double *)(base + o_sd);
+    H->dev_lz.ehhi_f = (const float *)(base + o_sf);
     *out = H;
     return KRY_OK;
 }

@@ -195,7 +195,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     char *base = (char *)H->ws;
     EvArgs<V> a{};
     a.b = b;
-    a.h = H->dev;
+    a.h = H->dev_lz;   // the Lanczos pass runs on H - s I
     a.W = (V *)(base + l.oW);
     a.ldW = l.ldW;
     a.U = (V *)(base + l.oU);
@@ -252,6 +252,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
     c.eta_cancel = 0.1;
     c.verify = H->orth_check;
+    c.shift = H->shift[0];
     if (opt && opt->ckpt) {
         c.ckpt_every = opt->ckpt_every;
         c.ckpt_cap = std::min(opt->ckpt_cap, 64);
@@ -465,7 +466,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     char *base = (char *)H->ws;
     EvArgsB<V> a{};
     a.b = b;
-    a.h = H->dev;
+    a.h = H->dev_lz;   // the Lanczos pass runs on H - s I
     a.W = (V *)(base + l.oW);
     a.ldW = l.ldW;
     a.U = (V *)(base + l.oU);
@@ -518,7 +519,10 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     hd.eta_cancel = 0.1;
     hd.verify = H->orth_check;
     hd.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
-    for (int k = 0; k < K; ++k) c->m_eff[k] = m;
+    for (int k = 0; k < K; ++k) {
+        c->m_eff[k] = m;
+        c->shift[k] = H->shift[k];
+    }
     const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)K;
     if (general) {
         hd.r0 = -1;

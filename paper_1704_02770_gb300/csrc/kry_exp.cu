@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
     const double tau_hi = fmin(remaining, XMAX / cr.y);
     const int K = cheb_degree(tau_hi * cr.y);
     cr = chebyshev_basis(sm, me, K);
-    const double c = cr.x, r = cr.y;
+    // T holds the coefficients of H - s I: the phase centre of exp(-i tau T) gets s back
+    const double c = cr.x + ctl->shift, r = cr.y;
     double *myJ = sm.jb + lane * (KMAX + 2);
 
     // ---- step-size ladder
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(32) k_exp_apply_b(ExpArgsB ea)
     double2 cr = gershgorin(sm, me);
     const int Kc = cheb_degree(tau * cr.y);
     cr = chebyshev_basis(sm, me, Kc);
-    const double c = cr.x, r = cr.y;
+    const double c = cr.x + ctl->shift[k], r = cr.y;   // T holds H_k - s_k I
     double *myJ = sm.jb + lane * (KMAX + 2);
     bessel_seq(tau * r, Kc, myJ);
     if (lane < me) {

@@ -124,6 +124,7 @@ struct KryCtlB {
     int dots[KBMAX];        // this realisation takes the dots of w (pass C1)
     int r0k[KBMAX];         // basis index of each realisation's initial state (hd.r0 >= 0)
     double pint[KBMAX];     // int_0^t_now P_k(t') dt' (temporal autocorrelation)
+    double shift[KBMAX];    // s_k of the Lanczos operator H_k - s_k I
 };
 
 template <class V>
@@ -188,6 +189,7 @@ struct KryCtl {
     int ckpt_every, n_ckpt, ckpt_cap;
     double ckpt_t[64];
     double pint;               // int_0^t_now P(t') dt' (temporal autocorrelation)
+    double shift;              // s of the Lanczos operator H - s I (T holds alpha - s)
 };
 
 // Dense output of whole vectors: psi(t_o) = sum_j Yout[o][j] W_j, written to out + o * ldOut.
@@ -280,6 +282,10 @@ struct kry_ham_s {
     std::vector<double> h;
     void *d_eh;
     kry::DevHam dev;
+    // the Lanczos pass works on H - s_k I (s_k = tr(H_k)/D): the same tables with s_k taken
+    // off the field energy, so that the diagonal offset does not dominate ||H v||
+    kry::DevHam dev_lz;
+    std::vector<double> shift;
     // evolution workspace (grown on demand, freed by kry_hamiltonian_destroy)
     void *ws;
     size_t ws_bytes;

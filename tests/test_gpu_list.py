@@ -214,3 +214,18 @@ def test_grad_list_equals_split_tables(kry):
         P, gh, gd, _ = H.grad(c["state"], 2.0, tol=1e-11, ckpt_every=4)
         out.append(np.r_[P, gh, gd])
     assert np.max(np.abs(out[0] - out[1])) <= 1e-10
+
+
+def test_ring_complex64_keeps_its_basis_orthogonal(kry):
+    """L = 55, N = 5 ring with Delta = 1, where the diagonal offset (about 8.75) dominates
+    ||H v||: the complex64 evolution keeps step sizes like complex128's (the Lanczos pass runs
+    on H - tr(H)/D) and agrees with it to the mixed-precision bar."""
+    B = kry.Basis(55, 5)
+    H = kry.Hamiltonian(B, 1.0, 1.0, workloads.aubry_andre_field(55, 2.0, 1.0, workloads.phases(7)[0]))
+    st = sum(1 << (11 * i) for i in range(5))
+    P128, s128 = H.return_probability(st, [10.0], tol=1e-10)
+    P64, s64 = H.return_probability(st, [10.0], tol=1e-7, dtype="c64")
+    print(f"[parity] ring L55 N5: Krylov steps c128 {s128['n_krylov_steps']}, c64 {s64['n_krylov_steps']}, "
+          f"|dP| {abs(P64[0] - P128[0]):.2e}")
+    assert s64["n_krylov_steps"] <= s128["n_krylov_steps"] + 2
+    assert abs(P64[0] - P128[0]) <= 1e-5
