@@ -80,3 +80,51 @@ def test_transposed_projection_is_caught():
 def test_wrong_hop_amplitude_is_caught():
     err = _P_vs_dense(lambda H: (lambda x: H.matvec(x) + 0.05 * (H.matvec(x) - x * 0)))
     assert err > 1e-6
+
+
+# ---- temporal autocorrelation and its exponent (Sec. 4)
+
+def _two_level_C_want(J, h, times):
+    d = h[0] - h[1]
+    W = np.sqrt(J * J + d * d)
+    A = J * J / (W * W)
+    return 1.0 - A / 2.0 + (A / 2.0) * np.sin(W * times) / (W * times)
+
+
+def _C_variant(H, psi0, times, slip):
+    """The oracle's spectral form of C(t) with one planted slip."""
+    E, U = np.linalg.eigh(H)
+    w = np.abs(U.conj().T @ psi0) ** 2
+    om = E[:, None] - E[None, :]
+    ww = w[:, None] * w[None, :]
+    out = []
+    for t in times:
+        if slip == "no_average":        # P(t) instead of its time average
+            out.append(float((ww * np.cos(om * t)).sum()))
+        elif slip == "no_division":     # the integral without the 1/t
+            out.append(float((ww * t * np.sinc(om * t / np.pi)).sum()))
+        elif slip == "half_frequency":  # sin(om t / 2) / (om t / 2)
+            out.append(float((ww * np.sinc(om * t / (2 * np.pi))).sum()))
+    return np.array(out)
+
+
+def test_planted_autocorrelation_slips_are_caught():
+    J, h = 1.3, [0.8, -0.3]
+    H = dense.hamiltonian_kron(2, J, 0.4, h, False, 1)
+    psi0 = np.array([1.0, 0.0])   # either site: P is the same for both
+    times = np.array([0.3, 1.7, 5.0, 23.0])
+    want = _two_level_C_want(J, h, times)
+    assert np.max(np.abs(dense.autocorrelation_dense(H, psi0, times) - want)) < 1e-13
+    for slip in ("no_average", "no_division", "half_frequency"):
+        assert np.max(np.abs(_C_variant(H, psi0, times, slip) - want)) > 1e-3, slip
+
+
+def test_planted_exponent_slips_are_caught():
+    from oracle import analysis
+    t = np.logspace(0, 3, 30)
+    C = 0.5 * t ** -0.83
+    assert abs(analysis.decay_exponent(t, C, 1.0, 1e3)[0] - 0.83) < 1e-12
+    slope = np.polyfit(np.log(t), np.log(C), 1)[0]
+    assert abs(slope - 0.83) > 1.0                     # the sign slip (gamma = +slope)
+    mixed = np.polyfit(np.log10(t), np.log(C), 1)[0]
+    assert abs(-mixed - 0.83) > 0.5                    # log10 t against ln C
