@@ -46,10 +46,13 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);   //
 // autocorrelation) to dst = [nodes | weights].
 int upload_gl(char *dst, cudaStream_t s)
 {
-    static std::vector<double> glx, glw;
-    if (glx.empty()) gauss_legendre(NGL, glx, glw);
-    KRY_CU(cudaMemcpyAsync(dst, glx.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
-    KRY_CU(cudaMemcpyAsync(dst + sizeof(double) * NGL, glw.data(), sizeof(double) * NGL, cudaMemcpyHostToDevice, s));
+    static const std::vector<double> gl = [] {   // [nodes | weights], built once (thread-safe)
+        std::vector<double> x, w;
+        gauss_legendre(NGL, x, w);
+        x.insert(x.end(), w.begin(), w.end());
+        return x;
+    }();
+    KRY_CU(cudaMemcpyAsync(dst, gl.data(), sizeof(double) * 2 * NGL, cudaMemcpyHostToDevice, s));
     return KRY_OK;
 }
 
