@@ -229,8 +229,18 @@ int kry_set_grid(kry_ham H, int dtype, int grid);
  * 1e-5 ||w|| (complex64). */
 int kry_set_orth_check(kry_ham H, int on);
 
-/* Bytes of device workspace kry_evolve allocates for (H, dtype, m); -1 on bad input. */
+/* Bytes of device workspace an evolution of H (single or batched by H's K) needs in dtype
+ * with Krylov dimension m and n_times output times, at the current launch shape (an autotuned
+ * grid can change it); -1 on bad input.  kry_workspace_size is the same for one output time. */
+int64_t kry_workspace_bytes(kry_ham H, int dtype, int m, int n_times);
 int64_t kry_workspace_size(kry_ham H, int dtype, int m);
+/* Give H a caller-owned device workspace (e.g. a torch tensor's memory): d_ws 256-byte
+ * aligned, `bytes` long, used by every later kry_evolve / kry_return_probability /
+ * kry_autocorrelation / kry_return_probability_states / kry_autotune call on H, never freed
+ * by the library.  A call that needs more than `bytes` (kry_workspace_bytes) returns
+ * KRY_EINVAL instead of allocating.  d_ws = NULL returns to library-managed memory.  The
+ * buffer must outlive its use; kry_grad keeps its own buffers. */
+int kry_set_workspace(kry_ham H, void *d_ws, int64_t bytes);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *kry_last_error(void);

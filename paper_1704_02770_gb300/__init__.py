@@ -56,6 +56,8 @@ SIGNATURES = {
     "kry_tridiag_expv": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_tridiag_expv_noalloc": (_i, [_dp, _dp, _i, _d, _d, _dp, _dp, _vp]),
     "kry_workspace_size": (_i64, [_vp, _i, _i]),
+    "kry_workspace_bytes": (_i64, [_vp, _i, _i, _i]),
+    "kry_set_workspace": (_i, [_vp, _vp, _i64]),
     "kry_autotune": (_i, [_vp, _i, _i, ctypes.c_uint64, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                           _dp, _i, ctypes.POINTER(_i), _vp]),
     "kry_set_grid": (_i, [_vp, _i, _i]),
@@ -176,6 +178,7 @@ class Hamiltonian:
         _check(load().kry_hamiltonian_set(basis._h, float(J), float(Delta), ptr, self.K,
                                           KRY_PBC if pbc else KRY_OBC, ctypes.byref(hnd)))
         self._h, self.basis, self.J, self.Delta, self.h, self.pbc = hnd, basis, J, Delta, hh, pbc
+        self._ws = None   # a caller-owned workspace tensor (set_workspace)
 
     def apply(self, x, out=None, stream=None):
         import torch
@@ -307,8 +310,19 @@ class Hamiltonian:
         return {k: dict(ms=float(ms[i]), bytes=float(by[i]), launches=int(n[i]))
                 for i, k in enumerate(self.KINDS)}
 
-    def workspace_size(self, dtype: str = "c128", m: int = 30) -> int:
-        return int(load().kry_workspace_size(self._h, KRY_C64 if dtype == "c64" else KRY_C128, m))
+    def workspace_size(self, dtype: str = "c128", m: int = 30, n_times: int = 1) -> int:
+        return int(load().kry_workspace_bytes(self._h, KRY_C64 if dtype == "c64" else KRY_C128, m, n_times))
+
+    def set_workspace(self, buf=None):
+        """Use a caller-owned device buffer (a CUDA tensor, kept referenced here) as the evolution
+        workspace, or None to return to library-managed memory (kry_set_workspace)."""
+        if buf is None:
+            _check(load().kry_set_workspace(self._h, None, 0))
+            self._ws = None
+            return
+        nbytes = buf.numel() * buf.element_size()
+        _check(load().kry_set_workspace(self._h, ctypes.c_void_p(buf.data_ptr()), nbytes))
+        self._ws = buf
 
     def close(self):
         if self._h:

@@ -36,6 +36,28 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int rl_in_smem(const DevBasis &b) { return (!b.list && b.Llo <= 15) ? 1 : 0; }
 
+void drop_graph(kry_ham_s *H);
+
+// The evolution workspace: grown on demand by the library, or the caller's buffer
+// (kry_set_workspace), which must already be large enough.
+int ensure_workspace(kry_ham_s *H, size_t bytes)
+{
+    if (H->ws && H->ws_bytes >= bytes) return KRY_OK;
+    if (H->ws_user) {
+        set_error("kry_evolve: the workspace given to kry_set_workspace holds %zu bytes; this call needs %zu",
+                  H->ws_bytes, bytes);
+        return KRY_EINVAL;
+    }
+    drop_graph(H);
+    if (H->ws) cudaFree(H->ws);
+    H->ws = nullptr;
+    H->ws_bytes = 0;
+    cudaError_t e = cudaMalloc(&H->ws, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+    H->ws_bytes = bytes;
+    return KRY_OK;
+}
+
 struct Layout {
     size_t ldW, oW, oU, oG, oPart, oCtl, oTimes, oP, oY, oC, oGL, bytes;
 };
@@ -184,15 +206,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     const int grid = grid_for(H, dtype, &gridH, &gridB);
     if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
     const Layout l = layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), n_times);
-    if (!H->ws || H->ws_bytes < l.bytes) {
-        drop_graph(H);
-        if (H->ws) cudaFree(H->ws);
-        H->ws = nullptr;
-        H->ws_bytes = 0;
-        cudaError_t e = cudaMalloc(&H->ws, l.bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
-        H->ws_bytes = l.bytes;
-    }
+    if (int rc = ensure_workspace(H, l.bytes)) return rc;
     if (!H->cap_stream) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
     if (!H->h_poll) KRY_CU(cudaMallocHost(&H->h_poll, sizeof(KryCtl)));
     char *base = (char *)H->ws;
@@ -455,15 +469,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     const int grid = grid_for_b(H, dtype, &gridB);
     if (grid <= 0) { set_error("kry_evolve: kernel configuration failed"); return KRY_ECUDA; }
     const Layout l = layout_b(H, dtype, m, std::max(grid, gridB), n_times);
-    if (!H->ws || H->ws_bytes < l.bytes) {
-        drop_graph(H);
-        if (H->ws) cudaFree(H->ws);
-        H->ws = nullptr;
-        H->ws_bytes = 0;
-        cudaError_t e = cudaMalloc(&H->ws, l.bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
-        H->ws_bytes = l.bytes;
-    }
+    if (int rc = ensure_workspace(H, l.bytes)) return rc;
     if (!H->cap_stream) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
     if (!H->h_poll) KRY_CU(cudaMallocHost(&H->h_poll, sizeof(KryCtl) > sizeof(KryHdrB) ? sizeof(KryCtl) : sizeof(KryHdrB)));
     char *base = (char *)H->ws;
@@ -645,7 +651,7 @@ extern "C" int kry_hamiltonian_destroy(kry_ham H)
 {
     if (!H) return KRY_OK;
     drop_graph(H);
-    if (H->ws) cudaFree(H->ws);
+    if (H->ws && !H->ws_user) cudaFree(H->ws);
     if (H->d_eh) cudaFree(H->d_eh);
     if (H->h_poll) cudaFreeHost(H->h_poll);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
@@ -668,13 +674,38 @@ extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *l
     return KRY_OK;
 }
 
-extern "C" int64_t kry_workspace_size(kry_ham H, int dtype, int m)
+extern "C" int64_t kry_workspace_bytes(kry_ham H, int dtype, int m, int n_times)
 {
-    if (!H || m < 1 || m > MMAX || (dtype != KRY_C128 && dtype != KRY_C64)) return -1;
+    if (!H || m < 1 || m > MMAX || n_times < 1 || (dtype != KRY_C128 && dtype != KRY_C64)) return -1;
+    if (H->K > 1) {
+        int gridB = 0;
+        const int grid = grid_for_b(H, dtype, &gridB);
+        if (grid <= 0) return -1;
+        return (int64_t)layout_b(H, dtype, m, std::max(grid, gridB), n_times).bytes;
+    }
     int gridH = 0, gridB = 0;
     const int grid = grid_for(H, dtype, &gridH, &gridB);
     if (grid <= 0) return -1;
-    return (int64_t)layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), 1).bytes;
+    return (int64_t)layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), n_times).bytes;
+}
+
+extern "C" int64_t kry_workspace_size(kry_ham H, int dtype, int m)
+{
+    return kry_workspace_bytes(H, dtype, m, 1);
+}
+
+extern "C" int kry_set_workspace(kry_ham H, void *d_ws, int64_t bytes)
+{
+    if (!H || (d_ws && bytes <= 0) || ((uintptr_t)d_ws & 255u)) {
+        set_error("kry_set_workspace: bad arguments (need H, and a 256-byte aligned buffer with bytes > 0)");
+        return KRY_EINVAL;
+    }
+    drop_graph(H);
+    if (H->ws && !H->ws_user) cudaFree(H->ws);
+    H->ws = d_ws;
+    H->ws_bytes = d_ws ? (size_t)bytes : 0;
+    H->ws_user = d_ws ? 1 : 0;
+    return KRY_OK;
 }
 
 extern "C" int kry_apply(kry_ham H, int dtype, const void *d_x, void *d_y, void *stream)

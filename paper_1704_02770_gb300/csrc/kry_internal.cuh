@@ -289,6 +289,7 @@ struct kry_ham_s {
     // evolution workspace (grown on demand, freed by kry_hamiltonian_destroy)
     void *ws;
     size_t ws_bytes;
+    int ws_user;                // ws belongs to the caller (kry_set_workspace): never freed here
     // cached CUDA graph of one Krylov step
     cudaGraphExec_t gexec;
     int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH;

@@ -63,6 +63,8 @@ def test_argument_validation_without_gpu(lib):
     assert b"C_out" in lib.kry_last_error()
     assert lib.kry_tridiag_expv(None, None, 0, 0.0, 0.0, None, None, None) == k.KRY_EINVAL
     assert lib.kry_workspace_size(None, 0, 30) == -1
+    assert lib.kry_workspace_bytes(None, 0, 30, 40) == -1
+    assert lib.kry_set_workspace(None, None, 0) == k.KRY_EINVAL
     assert lib.kry_basis_destroy(None) == k.KRY_OK
     assert lib.kry_hamiltonian_destroy(None) == k.KRY_OK
 

@@ -251,3 +251,28 @@ def test_config_L30_full_size(kry):
     err = float(np.max(np.abs(P128 - P64)))
     _report("L30 c64 vs c128 (t <= 0.5)", err)
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_caller_owned_workspace(kry, K):
+    """kry_set_workspace: a torch buffer of kry_workspace_bytes gives the same P as the
+    library's own workspace; a smaller one is refused; None returns to library memory."""
+    L, N = 14, 7
+    hs = [workloads.quasiperiodic_field(L, 1.0, p) for p in workloads.phases(12, K)]
+    times = workloads.log_times(12, 0.1, 20.0)
+    st = workloads.neel_state(L)
+    ref, _ = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs if K > 1 else hs[0]).return_probability(st, times)
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs if K > 1 else hs[0])
+    nb = H.workspace_size("c128", 30, n_times=len(times))
+    assert nb > 0
+    buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    H.set_workspace(buf)
+    P, _ = H.return_probability(st, times)
+    assert np.array_equal(np.asarray(P), np.asarray(ref))
+    H.set_workspace(buf[: nb // 2])
+    with pytest.raises(kry.KryError) as e:
+        H.return_probability(st, times)
+    assert e.value.code == kry.KRY_EINVAL
+    H.set_workspace(None)
+    P2, _ = H.return_probability(st, times)
+    assert np.array_equal(np.asarray(P2), np.asarray(ref))
