@@ -160,38 +160,6 @@ template <class V> struct DotAcc;
 template <> struct DotAcc<double2> : DotAccD {};
 template <> struct DotAcc<float2> : DotAccF {};
 
-// Streaming dots against a fixed tile y (the right operand, staged in shared memory once
-// per tile): complex64 keeps y expanded as (yx, yx, yy, yy) for the packed accumulator.
-// complex128 dots taken two elements at a time into two independent FP64 accumulators,
-// so consecutive fused multiply-adds do not wait on one another
-struct DotAccD2 {
-    DotAccD p, q;
-    __device__ __forceinline__ void add2(double2 a0, double2 b0, double2 a1, double2 b1)
-    {
-        p.add(a0, b0);
-        q.add(a1, b1);
-    }
-    __device__ __forceinline__ double2 value() const
-    {
-        const double2 x = p.value(), y = q.value();
-        return make_double2(x.x + y.x, x.y + y.y);
-    }
-};
-
-template <class V> struct TileDot;
-template <> struct TileDot<double2> {
-    using Acc = DotAccD2;
-    using Y = double2;
-    __device__ __forceinline__ static Y expand(double2 u) { return u; }
-    __device__ __forceinline__ static Y zero() { return make_double2(0.0, 0.0); }
-};
-template <> struct TileDot<float2> {
-    using Acc = DotAccF2;
-    using Y = float4;
-    __device__ __forceinline__ static Y expand(float2 u) { return make_float4(u.x, u.x, u.y, u.y); }
-    __device__ __forceinline__ static Y zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-};
-
 __device__ __forceinline__ double2 warp_sum(double2 v)
 {
 #pragma unroll
