@@ -185,6 +185,22 @@ def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
     return per * D * krylov_steps
 
 
+def fp64_pipe_ops(kind, D, m, krylov_steps, L, N, pbc):
+    """FP64 pipe instructions (per thread-element) of all launches of `kind`: a fused
+    multiply-add, a multiply and an add each occupy the pipe once, so the adds of the H.v
+    (two per gathered neighbour) cost as much pipe time as multiply-adds.  Pass A at index j:
+    2 per neighbour and 7 for the diagonal term and the scales, 4 per dot (j+1 of them) and 2
+    for ||u||^2; pass B: 4 per update (j+1) and 2 for ||w||^2."""
+    nb = 2.0 * N * (L - N) / ((L - 1) if pbc else L)
+    if kind == "passA":
+        per = sum(4 * (j + 1) + 2 + 7 + 2 * nb for j in range(m))
+    elif kind == "passB":
+        per = sum(4 * (j + 1) + 2 for j in range(m))
+    else:
+        return 0.0
+    return per * D * krylov_steps
+
+
 def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
     """Roofline of the dominant kernel kind over a profiled timed region.
 
@@ -214,10 +230,17 @@ def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
         mhz = clocks["sm_mhz"] or 2070.0
         fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
         ach_fl = fl / (prof[dom]["ms"] * 1e-3) / 1e12
+        ops = fp64_pipe_ops(dom, D, c["m"], steps, L, N, c["pbc"])
+        ach_ops = ops / (prof[dom]["ms"] * 1e-3) / 1e12
+        ops_peak = 152 * 2 * mhz * 1e6 / 1e12
+        pipe = {"achieved": ach_ops, "peak": ops_peak, "unit": "T FP64 instr/s", "frac": ach_ops / ops_peak,
+                "peak_source": "152 SMs x 2 FP64 instructions/clk x median SM clock",
+                "note": "adds occupy the pipe like multiply-adds; the H.v is add-heavy"}
         return {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
                 "traffic": tr, "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
+                "fp64_pipe_view": pipe,
                 "hbm_view": hbm, "per_kind": per, "kernel_time_share": share,
                 "profiled_region_s": prof.get("_sec"), "timing": TIMING_NOTE}
     return dict(bound="hbm", kernel=dom, traffic=tr, algo_bytes_per_launch=prof[dom]["bytes"] / nl,
