@@ -15,6 +15,8 @@ Modules:
               fermions, two-level formula)
   gradient -- dense Daleckii-Krein gradient of P(t) and finite differences
   analysis -- least-squares power-law exponent gamma of C(t) (Sec. 4)
+  moments  -- P(t) at early times from the power series of the exponential, for sectors
+              too large for the CSR oracle (L = 30)
 
 Parity status of each function is stated in its own docstring ("pinned by ...").
 """

@@ -151,3 +151,118 @@ void orc_spmv(int64_t D, const int64_t *rowptr, const int64_t *col, const double
         y[2 * r + 1] = im;
     }
 }
+
+/* ------------------------------------------------------------------ early-time moments
+ *
+ * The return amplitude of Eq. SP for a basis state s0, A(t) = <s0| exp(-iHt) |s0>, is the
+ * power series  sum_n (-it)^n mu_n / n!  in the moments mu_n = <s0| (H - c)^n |s0> of the
+ * shifted Hamiltonian (c = the diagonal element of s0; the shift multiplies A by a phase
+ * and leaves P unchanged).  v_k = (H - c)^k |s0> has its support on the states that k hops
+ * or fewer lead to from s0 (a hop exchanges the two sites of an antiparallel bond), so
+ *     mu_{2k} = <v_k, v_k>,   mu_{2k+1} = <v_k, v_{k+1}>
+ * for k < K need only the states within K hops of s0 ("the ball"), not the whole sector.
+ */
+
+static int cmp_u64(const void *a, const void *b)
+{
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Sort a[0..n) and drop repeats; returns the new length. */
+static int64_t sort_unique(uint64_t *a, int64_t n)
+{
+    if (n == 0) return 0;
+    qsort(a, (size_t)n, sizeof(uint64_t), cmp_u64);
+    int64_t k = 1;
+    for (int64_t i = 1; i < n; ++i)
+        if (a[i] != a[k - 1]) a[k++] = a[i];
+    return k;
+}
+
+/* mu[0..2K] for s0 and the number of states in its K-hop ball (*nball).  Returns 0, -1 on
+ * bad arguments or an allocation failure, -2 if a hopped state is missing from the ball
+ * (which cannot happen when the ball is built correctly). */
+int orc_moments(int L, double J, double Delta, const double *h, int pbc, uint64_t s0, int K,
+                double *mu, int64_t *nball)
+{
+    if (L < 1 || L > 62 || K < 0 || K > 64 || (L < 64 && (s0 >> L) != 0ull)) return -1;
+    const int nb = n_bonds(L, pbc);
+    uint64_t *all = (uint64_t *)malloc(sizeof(uint64_t)), *front = (uint64_t *)malloc(sizeof(uint64_t));
+    if (!all || !front) { free(all); free(front); return -1; }
+    all[0] = front[0] = s0;
+    int64_t nall = 1, nfront = 1;
+    for (int k = 1; k <= K; ++k) {
+        /* every state one hop away from the previous level, without repeats */
+        uint64_t *gen = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nfront * (nb > 0 ? nb : 1)));
+        if (!gen) { free(all); free(front); return -1; }
+        int64_t ng = 0;
+        for (int64_t q = 0; q < nfront; ++q) {
+            const uint64_t s = front[q];
+            for (int b = 0; b < nb; ++b) {
+                int i, j;
+                bond_sites(b, L, &i, &j);
+                if (((s >> i) & 1ull) != ((s >> j) & 1ull)) gen[ng++] = s ^ ((1ull << i) | (1ull << j));
+            }
+        }
+        ng = sort_unique(gen, ng);
+        /* the new level: generated states not yet in the ball (both lists ascending) */
+        uint64_t *nw = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(ng > 0 ? ng : 1));
+        uint64_t *merged = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nall + ng));
+        if (!nw || !merged) { free(gen); free(nw); free(merged); free(all); free(front); return -1; }
+        int64_t nn = 0, a = 0, g = 0, m = 0;
+        while (g < ng) {
+            if (a < nall && all[a] < gen[g]) { merged[m++] = all[a++]; continue; }
+            if (a < nall && all[a] == gen[g]) { merged[m++] = all[a++]; ++g; continue; }
+            nw[nn++] = gen[g];
+            merged[m++] = gen[g++];
+        }
+        while (a < nall) merged[m++] = all[a++];
+        free(gen);
+        free(all);
+        free(front);
+        all = merged;
+        nall = m;
+        front = nw;
+        nfront = nn;
+    }
+    free(front);
+    *nball = nall;
+    double *v = (double *)calloc((size_t)nall, sizeof(double));
+    double *w = (double *)calloc((size_t)nall, sizeof(double));
+    if (!v || !w) { free(v); free(w); free(all); return -1; }
+    const double c = orc_diag(s0, L, J, Delta, h, pbc);
+    v[orc_lookup(all, nall, s0)] = 1.0;
+    int rc = 0;
+    for (int k = 0; k <= K && rc == 0; ++k) {
+        double nv = 0.0;
+        for (int64_t r = 0; r < nall; ++r) nv += v[r] * v[r];
+        mu[2 * k] = nv;
+        if (k == K) break;
+        /* w = (H - c) v, pushed from the entries of v (all inside the (K-1)-hop ball) */
+        for (int64_t r = 0; r < nall; ++r) w[r] = 0.0;
+        for (int64_t r = 0; r < nall && rc == 0; ++r) {
+            if (v[r] == 0.0) continue;
+            const uint64_t s = all[r];
+            w[r] += (orc_diag(s, L, J, Delta, h, pbc) - c) * v[r];
+            for (int b = 0; b < nb; ++b) {
+                int i, j;
+                bond_sites(b, L, &i, &j);
+                if (((s >> i) & 1ull) == ((s >> j) & 1ull)) continue;
+                const int64_t q = orc_lookup(all, nall, s ^ ((1ull << i) | (1ull << j)));
+                if (q < 0) { rc = -2; break; }
+                w[q] += 0.5 * J * v[r];
+            }
+        }
+        double vw = 0.0;
+        for (int64_t r = 0; r < nall; ++r) vw += v[r] * w[r];
+        mu[2 * k + 1] = vw;
+        double *tmp = v;
+        v = w;
+        w = tmp;
+    }
+    free(v);
+    free(w);
+    free(all);
+    return rc;
+}

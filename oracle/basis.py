@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Pinned by: the worked example L=4, N=2 of Sec. 2 (tests/golden/basis_L4_N2.txt), the
 sector dimensions printed in Table I and Sec. 5 (tests/golden/dimensions.txt), brute-force
 enumeration of all 2^L integers, and a Kronecker-product construction of Eq. 1 in the
-full 2^L space (oracle.dense) for every L <= 10.
+full 2^L space (oracle.dense) for every L <= 10.  orc_moments (basis.c) is the engine of
+oracle.moments and is pinned there.
 """
 from __future__ import annotations
 
@@ -131,6 +132,10 @@ def row_apply(L, J, Delta, h, pbc, b: np.ndarray, x: np.ndarray, rows) -> np.nda
 
     Same construction as CSR (Eq. 1 by bit operations, column by binary lookup), one row
     at a time, for sizes whose full CSR matrix does not fit in host memory.
+
+    Pinned by: CSR.matvec on every row for several (L, N, boundary), and the Kronecker-
+    product H of oracle.dense on sampled rows of every sector for L <= 10
+    (tests/test_oracle_moments.py).
     """
     l = lib()
     h = np.ascontiguousarray(h, dtype=np.float64)

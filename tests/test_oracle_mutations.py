@@ -78,7 +78,14 @@ def test_transposed_projection_is_caught():
 
 
 def test_wrong_hop_amplitude_is_caught():
-    err = _P_vs_dense(lambda H: (lambda x: H.matvec(x) + 0.05 * (H.matvec(x) - x * 0)))
+    """The hop J/2 scaled by 1.05 alone; the diagonal of Eq. 1 (bond and field terms) kept."""
+    def factory(H):
+        rows = np.repeat(np.arange(H.D), np.diff(H.rowptr))
+        on = H.col == rows
+        diag = np.zeros(H.D)
+        diag[rows[on]] = H.val[on]
+        return lambda x: H.matvec(x) + 0.05 * (H.matvec(x) - diag * x)
+    err = _P_vs_dense(factory)
     assert err > 1e-6
 
 
