@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-l30", action="store_true", help="skip the L = 30 complex64 line")
+    ap.add_argument("--l30", action="store_true",
+                    help="only the L = 30 configuration in full: both fields, complex128 and complex64, e2e")
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the temporal autocorrelation, random-state ensemble and L = 55 ring lines")
     ap.add_argument("--form", default="c128", choices=["c128", "c64", "c64b"],
@@ -52,7 +55,7 @@ def parse():
                          "a short, fixed launch sequence for ncu captures")
     a = ap.parse_args()
     if a.kernels_only:
-        a.no_mixed = a.no_cpu_baseline = a.no_batched = a.no_widened = True
+        a.no_mixed = a.no_cpu_baseline = a.no_batched = a.no_widened = a.no_l30 = True
     return a
 
 
@@ -201,12 +204,16 @@ def fp64_pipe_ops(kind, D, m, krylov_steps, L, N, pbc):
     return per * D * krylov_steps
 
 
+MEASURED_FP64 = {}   # filled by run_ours from kry_measure_peaks on this GPU
+
+
 def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
     """Roofline of the dominant kernel kind over a profiled timed region.
 
-    complex128: every element costs FP64 arithmetic, and GB300's FP64 pipe (4 flop/clk/SM)
-    saturates before HBM, so the bound is the ALU; the HBM view is given beside it.
-    complex64: the bound is HBM."""
+    complex128: every element costs FP64 arithmetic, and GB300's FP64 pipe saturates before
+    HBM, so the bound is the ALU, against the FP64 multiply-add rate measured on this GPU in
+    the same run (kry_measure_peaks); the HBM view is given beside it.  complex64: the bound is
+    HBM."""
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
     dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
@@ -228,17 +235,24 @@ def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
         steps = prof[dom]["bytes"] / per_step
         fl = fp64_flops(dom, D, c["m"], steps, L, N, c["pbc"])
         mhz = clocks["sm_mhz"] or 2070.0
-        fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
+        if MEASURED_FP64.get("tflops"):
+            fp64_peak = MEASURED_FP64["tflops"]
+            src = ("measured in this run (kry_measure_peaks: FP64 multiply-add chains on every SM, "
+                   f"{MEASURED_FP64['tflops']:.3f} TFLOP/s; nominal 152 SMs x 4 flop/clk x {mhz:.0f} MHz = "
+                   f"{152 * 4 * mhz * 1e6 / 1e12:.3f})")
+        else:
+            fp64_peak = 152 * 4 * mhz * 1e6 / 1e12
+            src = "nominal: 152 SMs x 4 flop/clk x median SM clock (no measurement)"
         ach_fl = fl / (prof[dom]["ms"] * 1e-3) / 1e12
         ops = fp64_pipe_ops(dom, D, c["m"], steps, L, N, c["pbc"])
         ach_ops = ops / (prof[dom]["ms"] * 1e-3) / 1e12
-        ops_peak = 152 * 2 * mhz * 1e6 / 1e12
+        ops_peak = fp64_peak / 2.0
         pipe = {"achieved": ach_ops, "peak": ops_peak, "unit": "T FP64 instr/s", "frac": ach_ops / ops_peak,
-                "peak_source": "152 SMs x 2 FP64 instructions/clk x median SM clock",
+                "peak_source": "the measured multiply-add rate, one instruction each",
                 "note": "adds occupy the pipe like multiply-adds; the H.v is add-heavy"}
         return {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
-                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x median SM clock",
+                "peak_source": src,
                 "traffic": tr, "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
                 "fp64_pipe_view": pipe,
                 "hbm_view": hbm, "per_kind": per, "kernel_time_share": share,
@@ -268,6 +282,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     kry.load()
+    f64, f32 = kry.measure_peaks()
+    MEASURED_FP64.update(tflops=f64, fp32_tflops=f32)
     c = workloads.config(args.workload)
     L, N, times = c["L"], c["n_up"], c["times"]
     B = kry.Basis(L, N)
@@ -368,6 +384,15 @@ def run_ours(args):
                         "max_abs_dP_vs_fp64": float(np.max(np.abs(P64 - P128))),
                         "tol": 1e-7, "roofline": roofline(prof64, "c64", D, c, L, N, clocks)}
         out["gpu_launches"] += l64
+        # the FP64 form at the same stated accuracy (tol 1e-7): time to solution of both forms
+        sec7, hv7, l7, P7, st7, _ = timed("c128", 1e-7, profile=False)
+        u7, s7 = aggregate(D * hv7, sec7, world)
+        out["gpu_launches"] += l7
+        out["fp64_same_tol"] = {"tol": 1e-7, "value": u7 / s7, "unit": "state-updates/s",
+                                "ms_per_step": 1e3 * s7 / args.steps, "krylov_steps_per_step": st7["n_krylov_steps"],
+                                "max_abs_dP_vs_fp64_tol_1e-10": float(np.max(np.abs(P7 - P128)))}
+        out["mixed"]["time_to_solution_speedup_vs_fp64_same_tol"] = s7 / s64
+        out["mixed"]["krylov_steps_per_step"] = st64["n_krylov_steps"]
     # batched realisations: the K = 64 phase ensemble of L = 22 in one interleaved launch
     if not args.no_batched:
         cb = workloads.config("L22_batched_h1.5")
@@ -388,6 +413,24 @@ def run_ours(args):
             "disorder_avg_P_last": float(np.mean(Pb[-1])),
             "roofline": roofline(profb, "c64", Bb.dim * Kb, cb, cb["L"], cb["n_up"], clocks, traffic_key="b64_")}
         out["gpu_launches"] += lb
+        # time to solution against the FP64 form at the same tol: realisations 0 and 1 evolved
+        # one by one in complex128, scaled to the 64 of the ensemble
+        t64 = 0.0
+        for k in (0, 1):
+            Hk = kry.Hamiltonian(Bb, cb["J"], cb["Delta"], cb["h"][k], pbc=cb["pbc"])
+            Hk.return_probability(cb["state"], [0.1], dtype="c128", tol=1e-7)   # capture
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, stk = Hk.return_probability(cb["state"], cb["times"], dtype="c128", tol=1e-7)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 += e0.elapsed_time(e1) / 1e3
+            out["gpu_launches"] += stk["n_launches"]
+            del Hk
+        out["batched"]["time_to_solution_speedup_vs_fp64_same_tol"] = (t64 * Kb / 2.0) / sb
+        out["batched"]["fp64_same_tol_note"] = ("64 single complex128 evolutions at tol 1e-7, extrapolated from "
+                                                f"realisations 0 and 1 ({t64 / 2:.2f} s each)")
     if not args.no_widened:
         try:
             out["widened"] = widened(args, kry, workloads, H, c, D, out, world)
@@ -396,7 +439,17 @@ def run_ours(args):
             out["widened"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_batched:
         del Hb, Bb
-    cfg["autotune"] = {k: {"grid": v["grid"], "probe_ms": v["candidates"]} for k, v in tune.items()}
+    if not args.no_l30:
+        try:
+            out["l30"] = l30_leg(kry, workloads, world, tune, clocks, full=False)
+            out["gpu_launches"] += out["l30"].pop("_launches")
+        except Exception as e:   # the L = 30 line must not cost the headline line
+            out["l30"] = {"error": f"{type(e).__name__}: {e}"}
+    cfg["autotune"] = {k: {"shape": v["shape"], "probe_ms": v["candidates"],
+                           "default_shape_ms": next((ms for s_, ms in v["candidates"] if s_ == [0, 0, 0, 2, 0]), None)}
+                       for k, v in tune.items()}
+    cfg["measured_peaks"] = {"fp64_tflops": MEASURED_FP64.get("tflops"), "fp32_tflops": MEASURED_FP64.get("fp32_tflops"),
+                             "how": "kry_measure_peaks: independent multiply-add chains on every SM, CUDA events"}
     out["config"] = cfg
     if args.kernels_only:
         if rank == 0:
@@ -435,6 +488,83 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def l30_leg(kry, workloads, world, tune, clocks, full=False):
+    """The largest single-GPU configuration: L = 30, N_up = 15 (D = 155,117,520), Neel state,
+    m = 30, 40 log times to t = 100.  Default: the quasiperiodic field (h = 1.5) in complex64
+    (42 GB of Krylov workspace), one evolution after a short capture run.  full: both fields,
+    complex128 (84 GB) and complex64, and the end-to-end call with psi0 copied from pinned host
+    memory.  One evolution per case, with CUDA event nodes between the kernels for the
+    per-kind times (at this size their overhead is far below a kernel's duration)."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    res = {"workload": "L=30 N_up=15 D=155117520 PBC J=1 Delta=1, Neel psi0, m=30, 40 log times in [0.1,100]",
+           "timing": "one evolution per case after a capture run to t=0.1; per-kind times from event "
+                     "nodes in the same run"}
+    launches = 0
+    cases = [("L30_qp", "c64")] if not full else [(n, d) for n in ("L30_clean", "L30_qp") for d in ("c64", "c128")]
+    B = None
+    for name, dt in cases:
+        c = workloads.config(name)
+        if B is None:
+            B = kry.Basis(c["L"], c["n_up"])
+        D = B.dim
+        H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
+        if f"{dt}_K1" in tune:
+            H.set_shape(tune[f"{dt}_K1"]["shape"], dt)
+        tol = c["tol"] if dt == "c128" else 1e-7
+        H.return_probability(c["state"], [0.1], m=c["m"], tol=tol, dtype=dt)
+        H.profile(True)
+        H.return_probability(c["state"], [0.1], m=c["m"], tol=tol, dtype=dt)   # instrumented capture
+        H.profile(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P, st = H.return_probability(c["state"], c["times"], m=c["m"], tol=tol, dtype=dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        prof = H.profile_read()
+        prof["_sec"] = sec
+        H.profile(False)
+        u, s = aggregate(D * st["n_hv"], sec, world)
+        launches += st["n_launches"]
+        line = {"dtype": dt, "tol": tol, "value": u / s, "unit": "state-updates/s", "ms_per_step": 1e3 * s,
+                "krylov_steps": st["n_krylov_steps"], "hv": st["n_hv"], "P_first": float(P[0]),
+                "P_last": float(P[-1]),
+                "roofline": roofline(prof, dt, D, c, c["L"], c["n_up"], clocks, traffic_key="l30_")}
+        res[f"{name}_{dt}"] = line
+        if full and name == "L30_qp" and dt == "c64":
+            # end to end: psi0 from pinned host memory through kry_evolve, P back to the host
+            psi_h = torch.zeros(D, dtype=torch.complex64).pin_memory()
+            r0 = B.rank(torch.tensor([c["state"]], dtype=torch.int64, device="cuda")).item()
+            psi_h[r0] = 1.0
+            x = torch.empty(D, dtype=torch.complex64, device="cuda")
+            torch.cuda.synchronize()
+            e0.record(stream)
+            x.copy_(psi_h, non_blocking=True)
+            Pe, ste = H.evolve(x, c["times"], m=c["m"], tol=tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ue, se = aggregate(D * ste["n_hv"], e0.elapsed_time(e1) / 1e3, world)
+            launches += ste["n_launches"]
+            line["e2e"] = {"value": ue / se, "unit": "state-updates/s", "h2d_bytes_per_step": D * 8,
+                           "d2h_bytes_per_step": len(c["times"]) * 8,
+                           "max_abs_dP_vs_basis_state_call": float(np.max(np.abs(Pe - P)))}
+            del x, psi_h
+        H.close()
+        del H
+        torch.cuda.empty_cache()
+    if full:
+        for name in ("L30_clean", "L30_qp"):
+            a, b = res.get(f"{name}_c128"), res.get(f"{name}_c64")
+            if a and b:
+                b["speedup_vs_fp64"] = b["value"] / a["value"]
+    res["_launches"] = launches
+    return res
 
 
 def widened(args, kry, workloads, H, c, D, out, world):
@@ -622,9 +752,38 @@ def run_ncu_case(args):
                       "hv": st["n_hv"], "P": float(np.asarray(P).ravel()[0])}))
 
 
+def run_l30(args):
+    """python bench.py --l30: the L = 30 configuration in full (one JSON line)."""
+    import torch
+
+    import paper_1704_02770_gb300 as kry
+    import workloads
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    kry.load()
+    f64, f32 = kry.measure_peaks()
+    MEASURED_FP64.update(tflops=f64, fp32_tflops=f32)
+    # launch shapes from short probes of the L = 24 workload
+    c = workloads.config("L24_mixed")
+    H24 = kry.Hamiltonian(kry.Basis(c["L"], c["n_up"]), c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
+    tune = {f"{dt}_K1": H24.autotune(c["state"], 1.0, dtype=dt) for dt in ("c128", "c64")}
+    H24.close()
+    clk = ClockSampler(local).start()
+    res = l30_leg(kry, workloads, world, tune, {"sm_mhz": None}, full=True)
+    clocks = clk.stop()
+    res.pop("_launches")
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "l30": res, "clocks": clocks,
+                          "shapes": {k: v["shape"] for k, v in tune.items()},
+                          "measured_peaks": {"fp64_tflops": f64, "fp32_tflops": f32}}))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.ncu_case:
+    if a.l30:
+        run_l30(a)
+    elif a.ncu_case:
         run_ncu_case(a)
     elif a.impl == "reference":
         run_reference(a)

@@ -64,6 +64,7 @@ typedef struct kry_stats {
     double time_ms;          /* device time of the call (CUDA events)                        */
     double algo_bytes;       /* algorithmic HBM bytes of the call, by formula                 */
     int64_t n_launches;      /* kernels the call launched (including no-op launches)          */
+    int64_t n_second_dots;   /* second-pass dots taken (the test before a correction)         */
 } kry_stats;
 
 /* ---------------------------------------------------------------- basis (Sec. 2, Alg. 2)
@@ -161,8 +162,12 @@ int kry_return_probability_states(kry_ham H, int dtype, const uint64_t *psi0_sta
  * under -H); psi is checkpointed after every ckpt_every-th Krylov step of the forward
  * sweep and recomputed interval by interval during the backward sweep; the integral uses
  * composite 16-point Gauss-Legendre rules.  Outputs (host): P = P(t), dP_dh[L],
- * dP_dDelta.  Allocates its own temporary device buffers (a few vectors of D complex128
- * plus at most 64 checkpoints); synchronises `stream`.  m, tol: as kry_evolve. */
+ * dP_dDelta.  Allocates its own temporary device buffers: a few vectors of D complex128,
+ * the vectors at the quadrature nodes of one checkpoint interval, and the checkpoints.  The
+ * checkpoint buffer starts with room for 8; a forward sweep of more than 8 * ckpt_every
+ * Krylov steps grows it to (steps / ckpt_every) vectors and repeats the sweep.  KRY_ENOMEM
+ * (with the sizes in the message) when they do not fit: a larger ckpt_every needs fewer.
+ * Synchronises `stream`.  m, tol: as kry_evolve. */
 int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double tol, int ckpt_every,
              double *P, double *dP_dh, double *dP_dDelta, kry_stats *stats, void *stream);
 
@@ -184,8 +189,10 @@ int kry_tridiag_expv(const double *alpha, const double *beta, int m, double h, d
  * Its device scratch is one fixed array of about 1 KB, which every GPU that loads the
  * library keeps until the process exits.  That array caps m at 32; a larger m returns
  * KRY_EINVAL with a message naming the limit.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current) and keeps it;
- * make that first call before any stream capture.  All calls share the one array: calls
+ * array's device address (cudaGetSymbolAddress, with that device current) and keeps it for
+ * the CUDA context it was found in; a call from another context (for instance after
+ * cudaDeviceReset) looks it up again.  Make the first call on a device, and the first after a
+ * reset, before any stream capture.  All calls share the one array: calls
  * whose GPU work overlaps (two host threads, or two streams) race on it and must be
  * serialised by the caller.  Each call copies in every value its kernel reads, so nothing
  * left in the array by an earlier call affects the result.  Synchronises `stream`. */
@@ -206,19 +213,36 @@ int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, dou
 int kry_profile_enable(kry_ham H, int on);
 int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
 
-/* Launch-shape autotuner (not part of the paper's method).  Times a probe evolution of the
- * basis state probe_state to t_probe (reps replays after one warm-up, best kept) for each
- * candidate number of CTAs of the vector kernels: 0 (= the occupancy rule) and 1..4 times
- * the SM count; keeps the fastest for later calls on H with this dtype and returns it in
- * *grid_out.  cand_out / ms_out (host, max_cand entries) receive the candidates and their
- * times, *n_cand how many were tried.  The shape changes only the split of the work and
- * the order of the per-CTA partial sums. */
-int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_probe, int reps,
-                 int *grid_out, int *cand_out, double *ms_out, int max_cand, int *n_cand,
-                 void *stream);
-/* Set the number of CTAs of the vector kernels for H and dtype (0 = occupancy rule), e.g. a
- * value cached from an earlier kry_autotune. */
+/* Launch shape of the vector kernels (not part of the paper's method), per Hamiltonian and
+ * dtype, five ints:
+ *   shape[0] CTAs of the streaming kernels: 0 = the occupancy rule (whole SMs times the
+ *            resident CTAs of each kernel), else that many CTAs;
+ *   shape[1] gather form of the H.v: 0 = one hop at a time, 1 = the targets of up to eight hops
+ *            computed first and their loads issued together;
+ *   shape[2] dots of pass A: 0 = the next vector's rows loaded before the current vector's
+ *            products are accumulated (complex64), 1 = without that prefetch;
+ *   shape[3] rows per thread of the update pass: 1, 2 or 4;
+ *   shape[4] H.v of batched Hamiltonians (K > 1) in chunks of 8 or 16 realisations, so that
+ *            the gathered part of the vector fits in L2 (0 = all K at once).
+ * Parts 1, 2 and 4 change only the order of independent loads (the results are bitwise the
+ * same); parts 0 and 3 change which rows a thread or CTA sums into its partial norms and dots
+ * (the results agree to rounding).  Single-realisation evolutions use parts 0-3, batched ones
+ * parts 0 and 4.  New Hamiltonians start at {0, 0, 0, 2, 0}.
+ * kry_set_shape returns KRY_EINVAL for values outside those lists; kry_set_grid sets part 0. */
+int kry_set_shape(kry_ham H, int dtype, const int *shape);
+int kry_get_shape(kry_ham H, int dtype, int *shape);
 int kry_set_grid(kry_ham H, int dtype, int grid);
+
+/* Launch-shape autotuner (not part of the paper's method).  Times a probe evolution of the
+ * basis state probe_state to t_probe (reps replays after one capture run, best kept) for
+ * candidate shapes, one part after another with the other parts at their best so far: part 0
+ * over {0, 1, 2, 3, 4 x the SM count}, then part 1 over {0, 1}, part 2 over {0, 1}, part 3 over
+ * {2, 1, 4} (K > 1: part 0, then part 4 over {0, 16, 8}).  Keeps the fastest for later calls on
+ * H with this dtype and returns it in shape_out[5].  cand_out (host, [max_cand][5]) and ms_out
+ * ([max_cand]) receive the shapes tried and their times, *n_cand how many were stored. */
+int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_probe, int reps,
+                 int *shape_out, int *cand_out, double *ms_out, int max_cand, int *n_cand,
+                 void *stream);
 
 /* Reorthogonalisation check (a diagnostic; single-realisation evolutions).  Every new
  * Lanczos vector is orthogonalised against all previous ones by one classical Gram-Schmidt
@@ -226,7 +250,12 @@ int kry_set_grid(kry_ham H, int dtype, int grid);
  * pass is made only when that pass cancelled most of the vector (||w|| < 0.1 ||H v_j||).
  * With on = 1 the dots of every new vector with all previous ones are measured after each
  * pass (kry_stats.max_orth_loss) and subtracted when they exceed 1e-12 ||w|| (complex128) or
- * 1e-5 ||w|| (complex64). */
+ * 1e-5 ||w|| (complex64); with on = 2 they are subtracted after every update (classical
+ * Gram-Schmidt applied twice to every vector, as in the oracle).  Besides the cancellation
+ * test, the second pass is also taken when the lengths of u = H v_j, of its projections
+ * c = V^H u and of w = u - V c disagree with Pythagoras, | ||w||^2 - (||u||^2 - ||c||^2) |
+ * > 1e-12 (1e-5) ||c|| ||w|| plus the storage-precision noise, a sign that V has lost
+ * orthogonality.  Returns KRY_EINVAL for other values of on. */
 int kry_set_orth_check(kry_ham H, int on);
 
 /* Bytes of device workspace an evolution of H (single or batched by H's K) needs in dtype
@@ -241,6 +270,14 @@ int64_t kry_workspace_size(kry_ham H, int dtype, int m);
  * KRY_EINVAL instead of allocating.  d_ws = NULL returns to library-managed memory.  The
  * buffer must outlive its use; kry_grad keeps its own buffers. */
 int kry_set_workspace(kry_ham H, void *d_ws, int64_t bytes);
+
+/* Measured arithmetic peaks of the current device (a measurement aid, not part of the paper's
+ * method): FP64 and FP32 fused multiply-add throughput in TFLOP/s (2 flops per multiply-add),
+ * from independent chains of multiply-adds on every SM timed with CUDA events on `stream`
+ * (best of three after a warm-up).  Allocates and frees 4 bytes of device memory; takes about
+ * 0.3 s; synchronises `stream`.  The complex128 kernels are bound by the FP64 rate on GB300,
+ * and this is the denominator of their roofline. */
+int kry_measure_peaks(double *fp64_tflops, double *fp32_tflops, void *stream);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char *kry_last_error(void);

@@ -28,7 +28,7 @@ class Stats(ctypes.Structure):
                 ("n_second_pass", ctypes.c_int64), ("n_breakdowns", ctypes.c_int64),
                 ("err_estimate", ctypes.c_double), ("max_orth_loss", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("algo_bytes", ctypes.c_double),
-                ("n_launches", ctypes.c_int64)]
+                ("n_launches", ctypes.c_int64), ("n_second_dots", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -61,9 +61,12 @@ SIGNATURES = {
     "kry_autotune": (_i, [_vp, _i, _i, ctypes.c_uint64, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                           _dp, _i, ctypes.POINTER(_i), _vp]),
     "kry_set_grid": (_i, [_vp, _i, _i]),
+    "kry_set_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "kry_get_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "kry_set_orth_check": (_i, [_vp, _i]),
     "kry_profile_enable": (_i, [_vp, _i]),
     "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "kry_measure_peaks": (_i, [_dp, _dp, _vp]),
     "kry_last_error": (ctypes.c_char_p, []),
 }
 
@@ -248,9 +251,10 @@ class Hamiltonian:
 
     def autotune(self, state: int, t_probe: float, dtype: str = "c128", m: int = 30, reps: int = 2,
                  cache: str | None = None, stream=None):
-        """Pick the CTA count of the vector kernels by timing a probe evolution (kry_autotune).
+        """Pick the launch shape of the vector kernels by timing probe evolutions (kry_autotune).
 
-        With `cache` (a JSON file path), a result stored for the same sector, K, dtype, m
+        Returns {"shape": [grid, hv form, dots form, update rows, batched chunk], "candidates": [[shape, ms],
+        ...]}.  With `cache` (a JSON file path), a result stored for the same sector, K, dtype, m
         and GPU is reused instead of measuring, and new results are added to the file."""
         import json
         import torch
@@ -261,24 +265,38 @@ class Hamiltonian:
         if cache and os.path.exists(cache):
             with open(cache) as f:
                 db = json.load(f)
-            if key in db:
-                _check(load().kry_set_grid(self._h, code, int(db[key]["grid"])))
+            if key in db and "shape" in db[key]:
+                self.set_shape(db[key]["shape"], dtype)
                 return db[key]
-        g, n = ctypes.c_int(0), ctypes.c_int(0)
-        cand = (ctypes.c_int * 8)()
-        ms = (ctypes.c_double * 8)()
+        nmax = 16
+        shp = (ctypes.c_int * 5)()
+        cand = (ctypes.c_int * (5 * nmax))()
+        ms = (ctypes.c_double * nmax)()
+        n = ctypes.c_int(0)
         _check(load().kry_autotune(self._h, code, m, ctypes.c_uint64(state), float(t_probe), reps,
-                                   ctypes.byref(g), cand, ms, 8, ctypes.byref(n), _stream(stream)))
-        res = {"grid": g.value, "candidates": {int(cand[i]): float(ms[i]) for i in range(n.value)}}
+                                   shp, cand, ms, nmax, ctypes.byref(n), _stream(stream)))
+        res = {"shape": list(shp), "candidates": [[list(cand[5 * i:5 * i + 5]), float(ms[i])]
+                                                  for i in range(n.value)]}
         if cache:
             db[key] = res
             with open(cache, "w") as f:
                 json.dump(db, f, indent=1)
         return res
 
-    def orth_check(self, on: bool = True):
-        """Measure (and subtract when needed) <v_i, w> after every Lanczos update."""
-        _check(load().kry_set_orth_check(self._h, 1 if on else 0))
+    def set_shape(self, shape, dtype: str = "c128"):
+        """Launch shape [grid, hv form, dots form, update rows, batched chunk] (kry_set_shape)."""
+        arr = (ctypes.c_int * 5)(*[int(x) for x in shape])
+        _check(load().kry_set_shape(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, arr))
+
+    def get_shape(self, dtype: str = "c128"):
+        arr = (ctypes.c_int * 5)()
+        _check(load().kry_get_shape(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, arr))
+        return list(arr)
+
+    def orth_check(self, on=True):
+        """Measure (and subtract when needed) <v_i, w> after every Lanczos update; on = 2
+        subtracts them after every update (kry_set_orth_check)."""
+        _check(load().kry_set_orth_check(self._h, int(on)))
 
     def set_grid(self, grid: int, dtype: str = "c128"):
         _check(load().kry_set_grid(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, grid))
@@ -348,6 +366,13 @@ def tridiag_expv(alpha, beta, h: float, tau: float, stream=None):
     return y[0::2] + 1j * y[1::2], float(err[0])
 
 
+def measure_peaks(stream=None):
+    """(FP64, FP32) fused multiply-add throughput of the current GPU in TFLOP/s (kry_measure_peaks)."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(load().kry_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
+    return f64.value, f32.value
+
+
 def decay_exponent(times, C, t_min: float, t_max: float):
     """(gamma, log a) of the fit C(t) ~ a t^-gamma over t_min <= t <= t_max (kry_decay_exponent)."""
     t, tp = _host_doubles(times)
@@ -364,26 +389,37 @@ def _return_probability_fn():
 
     class ReturnProbability(torch.autograd.Function):
         """P(t) = |<psi0| exp(-iHt) |psi0>|^2 as a differentiable function of the on-site
-        fields h [L] and of Delta (float64 CPU tensors).  Forward and backward both run
-        kry_grad on the GPU: the backward pass returns grad_output * dP/dh and
-        grad_output * dP/dDelta computed by the adjoint (costate) evolution."""
+        fields h [L] and of Delta (float64 tensors on any device; the values are read on the
+        host).  When a gradient is wanted, forward runs kry_grad on the GPU (P and the adjoint
+        (costate) evolution) and backward returns grad_output * dP/dh and grad_output *
+        dP/dDelta on the inputs' devices; otherwise forward runs only the evolution of P."""
 
         @staticmethod
-        def forward(ctx, h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every):
+        def forward(ctx, h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every, want_grad):
             H = Hamiltonian(basis, float(J), float(Delta.item()), h.detach().cpu().numpy(), pbc=pbc)
-            P, gh, gd, _ = H.grad(state, t, m=m, tol=tol, ckpt_every=ckpt_every)
-            H.close()
-            ctx.save_for_backward(torch.from_numpy(gh), torch.tensor(gd, dtype=torch.float64))
-            return torch.tensor(P, dtype=torch.float64)
+            try:
+                if want_grad:
+                    P, gh, gd, _ = H.grad(state, t, m=m, tol=tol, ckpt_every=ckpt_every)
+                    ctx.save_for_backward(torch.from_numpy(gh).to(h.device),
+                                          torch.tensor(gd, dtype=torch.float64, device=Delta.device))
+                else:
+                    Pv, _ = H.return_probability(state, [t], m=m, tol=tol)
+                    P = float(Pv[0])
+            finally:
+                H.close()
+            return torch.tensor(P, dtype=torch.float64, device=h.device)
 
         @staticmethod
         def backward(ctx, g):
             gh, gd = ctx.saved_tensors
-            return g * gh, g * gd, None, None, None, None, None, None, None, None
+            return g.to(gh.device) * gh, g.to(gd.device) * gd, None, None, None, None, None, None, None, None, None
 
     return ReturnProbability
 
 
 def return_probability(h, Delta, basis, J, state, t, pbc=True, m=30, tol=1e-10, ckpt_every=8):
-    """Differentiable P(t): h a float64 tensor [L], Delta a float64 scalar tensor."""
-    return _return_probability_fn().apply(h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every)
+    """Differentiable P(t): h a float64 tensor [L], Delta a float64 scalar tensor.  The adjoint
+    runs only when grad mode is on and h or Delta requires a gradient."""
+    import torch
+    want = torch.is_grad_enabled() and (h.requires_grad or Delta.requires_grad)
+    return _return_probability_fn().apply(h, Delta, basis, J, state, t, pbc, m, tol, ckpt_every, want)

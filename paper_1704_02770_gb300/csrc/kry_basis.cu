@@ -246,13 +246,17 @@ extern "C" int kry_basis_create(int L, int n_up, kry_basis *out)
     cudaError_t e = cudaMalloc(&b->d_tab, bytes);
     if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaMalloc(tables)"); }
     char *base = (char *)b->d_tab;
-    cudaMemcpy(base + o_blk, blk.data(), sizeof(uint32_t) * nhi, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_rl, ranklo.data(), sizeof(uint16_t) * nlo, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_ll, lolist.data(), sizeof(uint16_t) * nlo, cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_ko, koff.data(), sizeof(uint32_t) * (Llo + 2), cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_bs, bsz.data(), sizeof(uint32_t) * (Llo + 1), cudaMemcpyHostToDevice);
-    cudaMemcpy(base + o_ts, tstart.data(), sizeof(uint32_t) * tstart.size(), cudaMemcpyHostToDevice);
-    e = cudaMemset(base + o_er, 0, 16);
+    const struct { size_t off; const void *src; size_t n; } up[] = {
+        {o_blk, blk.data(), sizeof(uint32_t) * nhi},
+        {o_rl, ranklo.data(), sizeof(uint16_t) * nlo},
+        {o_ll, lolist.data(), sizeof(uint16_t) * nlo},
+        {o_ko, koff.data(), sizeof(uint32_t) * (Llo + 2)},
+        {o_bs, bsz.data(), sizeof(uint32_t) * (Llo + 1)},
+        {o_ts, tstart.data(), sizeof(uint32_t) * tstart.size()},
+    };
+    for (const auto &u : up)
+        if (e == cudaSuccess) e = cudaMemcpy(base + u.off, u.src, u.n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(base + o_er, 0, 16);
     if (e != cudaSuccess) { cudaFree(b->d_tab); delete b; return cuda_fail(e, "table upload"); }
     DevBasis &d = b->dev;
     d.blk = (const uint32_t *)(base + o_blk);
@@ -364,6 +368,7 @@ static int ham_set_list(kry_basis b, double J, double Delta, const double *h, in
     for (size_t i = 0; i < n8; ++i) ehf[i] = (float)eh[i];
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
+    default_shape(H);
     fill_dev_ham(H->dev, J, Delta, L, K, boundary);
     // shifted copy for the Lanczos pass: s_k taken off the byte-0 entries
     H->shift.resize(K);
@@ -442,6 +447,7 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
     }
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
+    default_shape(H);
     fill_dev_ham(H->dev, J, Delta, L, K, boundary);
     // shifted copy of the upper-bit table for the Lanczos pass: s_k taken off every entry
     H->shift.resize(K);

@@ -27,14 +27,14 @@ struct SmemHeadB {
 };
 
 // Row r of H x for every realisation: the rank arithmetic is the same for all k, the
-// lanes of the warp run over k = lane + 32 q.
+// lanes of the warp run over k = lane + 32 q (k0 = lane), or one realisation k0 per lane.
 template <class V, int KQ>
 __device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
                                          int K, uint32_t hi, uint32_t off, int klo,
-                                         const uint32_t *koff_s, const uint16_t *rl, V out[KQ])
+                                         const uint32_t *koff_s, const uint16_t *rl, V out[KQ], int k0)
 {
     using R = typename VT<V>::R;
-    const int lane = threadIdx.x & 31;
+    const int lane = k0;
     const int Llo = b.Llo, L = b.L;
     const uint32_t pos = koff_s[klo] + off;
     const uint32_t lo = __ldg(b.lolist + pos);
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NTHR) k_apply_b(DevBasis b, DevHam hm, int K, 
             int klo;
             tile_unrank(b, hd->bsz, r0, rr, hi, off, klo);
             V u[KQ];
-            hv_row_b<V, KQ>(b, hm, x, K, hi, off, klo, hd->koff, rl, u);
+            hv_row_b<V, KQ>(b, hm, x, K, hi, off, klo, hd->koff, rl, u, lane);
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 const int k = lane + 32 * q;
@@ -165,12 +165,54 @@ __global__ void __launch_bounds__(NTHR) k_hv_b(EvArgsB<V> a, int jj)
             int klo;
             tile_unrank(a.b, hd->bsz, r0, rr, hi, off, klo);
             V u[KQ];
-            hv_row_b<V, KQ>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u);
+            hv_row_b<V, KQ>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u, lane);
 #pragma unroll
             for (int q = 0; q < KQ; ++q) {
                 const int k = lane + 32 * q;
                 if (k < K) a.U[(size_t)(r0 + rr) * K + k] = scale(u[q], sg[q]);
             }
+        }
+    }
+}
+
+// Part 1 in chunks of KCH realisations: the work items are (chunk, tile) pairs in chunk-major
+// order and a warp holds 32 / KCH states, KCH lanes each.  The CTAs sweep all tiles of one
+// chunk before the next, so the gathered part of W_j (D x KCH amplitudes, e.g. 90 MB for
+// L = 22 and KCH = 16 in complex64) stays in L2 while its rows are gathered about eleven
+// times each; without chunks the whole [D][K] block (361 MB at K = 64) exceeds L2 and
+// gathered rows come from HBM several times.  The rank arithmetic is repeated per chunk.
+// Same hop order per amplitude as k_hv_b: the same bits.
+template <class V, int KCH>
+__global__ void __launch_bounds__(NTHR) k_hv_bc(EvArgsB<V> a, int jj)
+{
+    using R = typename VT<V>::R;
+    KryCtlB *ctl = a.ctl;
+    if (ctl->hd.done || jj >= ctl->hd.m_run) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemHeadB *hd = (SmemHeadB *)smem;
+    uint16_t *rl_s = (uint16_t *)(smem + sizeof(SmemHeadB));
+    stage_tables(a.b, hd->koff, hd->bsz, rl_s, a.rl_smem);
+    __syncthreads();
+    const uint16_t *rl = a.rl_smem ? rl_s : a.b.ranklo;
+    constexpr int SPW = 32 / KCH;   // states per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, K = a.K;
+    const int sub = lane / KCH, kk = lane % KCH;
+    const V *x = a.W + (size_t)jj * a.ldW;
+    const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
+    const uint32_t nch = (uint32_t)((K + KCH - 1) / KCH);
+    for (uint32_t item = blockIdx.x; item < nch * ntiles; item += gridDim.x) {
+        const uint32_t ch = item / ntiles, tile = item - ch * ntiles;
+        const int k = (int)ch * KCH + kk;
+        const R sg = (k < K) ? (R)ctl->sigma[jj][k] : (R)0;
+        const uint32_t r0 = tile * TROWS;
+        for (int rr = warp * SPW + sub; rr < TROWS; rr += (NTHR / 32) * SPW) {
+            if (r0 + rr >= D) break;
+            uint32_t hi, off;
+            int klo;
+            tile_unrank(a.b, hd->bsz, r0, rr, hi, off, klo);
+            V u[1];
+            hv_row_b<V, 1>(a.b, a.h, x, K, hi, off, klo, hd->koff, rl, u, k);
+            if (k < K) a.U[(size_t)(r0 + rr) * K + k] = scale(u[0], sg);
         }
     }
 }
@@ -602,11 +644,27 @@ int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
     }
     const size_t sH = hv_b_smem(a.b, a.rl_smem);
     const uint32_t ntiles = (a.b.D + TROWS - 1) / TROWS;
-    KRY_KQ_SWITCH(a.Kp, {
+    auto hv_grid = [&](auto kernel, uint32_t items) {
         int oh = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oh, k_hv_b<V, KQ>, NTHR, sH);
-        const int gh = (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count_b() * std::max(1, oh))));
-        k_hv_b<V, KQ><<<gh, NTHR, sH, s>>>(a, jj);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oh, kernel, NTHR, sH);
+        return (int)std::max<uint32_t>(1u, std::min<uint32_t>(items, (uint32_t)(sm_count_b() * std::max(1, oh))));
+    };
+    if (a.kch == 8 || a.kch == 16) {   // chunks of realisations (launch shape part 4)
+        const uint32_t items = ntiles * (uint32_t)((a.K + a.kch - 1) / a.kch);
+        if (a.kch == 8) {
+            if (int rc = set_smem(k_hv_bc<V, 8>, sH)) return rc;
+            k_hv_bc<V, 8><<<hv_grid(k_hv_bc<V, 8>, items), NTHR, sH, s>>>(a, jj);
+        } else {
+            if (int rc = set_smem(k_hv_bc<V, 16>, sH)) return rc;
+            k_hv_bc<V, 16><<<hv_grid(k_hv_bc<V, 16>, items), NTHR, sH, s>>>(a, jj);
+        }
+        KRY_CU(cudaGetLastError());
+        KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
+        KRY_CU(cudaGetLastError());
+        return KRY_OK;
+    }
+    KRY_KQ_SWITCH(a.Kp, {
+        k_hv_b<V, KQ><<<hv_grid(k_hv_b<V, KQ>, ntiles), NTHR, sH, s>>>(a, jj);
         k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj);
     });
     KRY_CU(cudaGetLastError());

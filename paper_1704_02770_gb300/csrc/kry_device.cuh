@@ -295,4 +295,78 @@ __device__ __forceinline__ V hv_row_scaled(const DevBasis &b, const DevHam &hm, 
     return axpby(sigma * d, __ldg(x + base + off), sigma_halfJ, acc);
 }
 
+// The same row as hv_row_scaled with the gathers issued in chunks: the targets of up to
+// eight hops are computed first and their loads issued together, so a thread has up to eight
+// gathers in flight instead of one (a warp issues in order, and the loop of hv_row_scaled
+// waits for each gathered value before it computes the next target).  Zeros stand in for the
+// bonds that do not hop and the terms are added in the same order as in hv_row_scaled, so the
+// result is bitwise the same.  Needs Llo, Lhi <= 16 (L <= 32).
+template <class V>
+__device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
+                                            uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
+                                            const uint16_t *rl, const typename VT<V>::R *dz,
+                                            typename VT<V>::R sigma, typename VT<V>::R sigma_halfJ)
+{
+    using R = typename VT<V>::R;
+    const int Llo = b.Llo, L = b.L;
+    const uint32_t pos = koff_s[klo] + off;
+    const uint32_t lo = __ldg(b.lolist + pos);
+    const uint32_t s = (hi << Llo) | lo;
+    const uint32_t base = __ldg(b.blk + hi);
+    const uint32_t lomask = (1u << Llo) - 1u;
+    const uint32_t obc = (L >= 2) ? ((1u << (L - 1)) - 1u) : 0u;
+    const uint32_t anti = (s ^ (s >> 1)) & obc;
+    const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
+    const R d = dz[__popc(anti) + (int)wrap] + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
+    const V xr = __ldg(x + base + off);
+    V acc = VT<V>::zero();
+    const uint32_t a = anti & ((1u << (Llo - 1)) - 1u);    // bonds inside the lower part
+#pragma unroll
+    for (int c0 = 0; c0 < 16; c0 += 8) {
+        if (!((a >> c0) & 0xFFu)) continue;
+        V v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int p = c0 + u;
+            v[u] = ((a >> p) & 1u) ? __ldg(x + base + rl[(lo ^ (3u << p)) & lomask]) : VT<V>::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if ((a >> (c0 + u)) & 1u) acc = acc + v[u];
+    }
+    const bool cross = b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u);   // bond joining the two parts
+    const uint32_t ah = anti >> Llo;                               // bonds inside the upper part
+    const uint32_t himask = (1u << b.Lhi) - 1u;   // (the masks keep every index in range)
+    V vc = VT<V>::zero();
+    if (cross) {
+        const uint32_t s2 = s ^ (3u << (Llo - 1));
+        vc = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    V vr = VT<V>::zero();
+    if (wrap) {                                                    // ring bond (L-1, 0)
+        const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
+        vr = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+    }
+    if (cross) acc = acc + vc;
+#pragma unroll
+    for (int c0 = 0; c0 < 16; c0 += 8) {
+        if (!((ah >> c0) & 0xFFu)) continue;
+        uint32_t t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = c0 + u;
+            t[u] = ((ah >> q) & 1u) ? __ldg(b.blk + ((hi ^ (3u << q)) & himask)) : 0u;
+        }
+        V v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            v[u] = ((ah >> (c0 + u)) & 1u) ? __ldg(x + t[u] + off) : VT<V>::zero();
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if ((ah >> (c0 + u)) & 1u) acc = acc + v[u];
+    }
+    if (wrap) acc = acc + vr;
+    return axpby(sigma * d, xr, sigma_halfJ, acc);
+}
+
 }  // namespace kry

@@ -38,6 +38,16 @@ int rl_in_smem(const DevBasis &b) { return (!b.list && b.Llo <= 15) ? 1 : 0; }
 
 void drop_graph(kry_ham_s *H);
 
+// Timing events of one call, released on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // The evolution workspace: grown on demand by the library, or the caller's buffer
 // (kry_set_workspace), which must already be large enough.
 int ensure_workspace(kry_ham_s *H, size_t bytes)
@@ -104,10 +114,11 @@ struct EvOpts {
     void *vec_out = nullptr;   // [n_times][ldOut] elements
     size_t ldOut = 0;
     void *ckpt = nullptr;      // [ckpt_cap][ldC] elements
+    double *d_ckpt_t = nullptr;   // device [ckpt_cap]: checkpoint times
     size_t ldC = 0;
     int ckpt_every = 0, ckpt_cap = 0;
-    int n_ckpt = 0;            // out
-    double ckpt_t[64] = {};    // out
+    int n_ckpt = 0;            // out: checkpoints written (at most ckpt_cap)
+    std::vector<double> ckpt_t;   // out: their times
     double *C_out = nullptr;   // host [n_times]: temporal autocorrelation C(t_o)
 };
 
@@ -119,7 +130,7 @@ int grid_for(const kry_ham_s *H, int dtype, int *gridH, int *gridB)
     const int rl = rl_in_smem(b);
     const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl, gridH, gridB)
                                    : vector_grid<double2>(b, rl, gridH, gridB);
-    const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
+    const int ov = H->shape[dtype == KRY_C64 ? 1 : 0][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return (g > 0 && ov > 0) ? ov : g;   // vector_grid also sets the kernels' smem limits
 }
@@ -159,18 +170,58 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         }
         ++k;
     };
+    // The second Gram-Schmidt pass (pass C: its dots, then the subtraction) is the body of a
+    // conditional node after pass B, whose last CTA sets the node's value: the pass costs
+    // nothing in the Lanczos indices where it is not needed.  The kernel after a conditional
+    // node is launched without programmatic dependence (that only links two kernels).
+    cudaStream_t cs2 = H->cap_stream2;
+    int after_cond = 0;
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
         mark();
-        rc = launch_hv<V>(a, jj, gridH, cs);
+        rc = launch_hv<V>(a, jj, gridH, cs, after_cond ? 0 : 1);
         if (rc == KRY_OK) rc = launch_dots<V>(a, 0, jj, grid, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, gridB, cs);
+        EvArgs<V> ab = a;
+        cudaGraph_t cg = nullptr;
+        if (rc == KRY_OK) {
+            cudaStreamCaptureStatus cst;
+            cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg);
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ab.cond, cg, 0, cudaGraphCondAssignDefault);
+            if (e != cudaSuccess) rc = cuda_fail(e, "conditional handle");
+            ab.use_cond = 1;
+        }
+        if (rc == KRY_OK) rc = launch_lincomb<V>(ab, 0, jj, gridB, cs);
         mark();
-        if (rc == KRY_OK) rc = launch_dots<V>(a, 1, jj, grid, cs);
-        if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, gridB, cs);
+        if (rc == KRY_OK) {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *edges = nullptr;
+            size_t nd = 0;
+            cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &edges, &nd);
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = ab.cond;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, cg, deps, edges, nd, &cp);
+            if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(cs2, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) rc = cuda_fail(e, "conditional node");
+            if (rc == KRY_OK) {
+                rc = launch_dots<V>(a, 1, jj, grid, cs2, 0);
+                if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, gridB, cs2, 0);
+                cudaGraph_t body = nullptr;
+                e = cudaStreamEndCapture(cs2, &body);
+                if (rc == KRY_OK && e != cudaSuccess) rc = cuda_fail(e, "conditional body capture");
+            }
+            after_cond = 1;
+        }
     }
     mark();
-    if (rc == KRY_OK) rc = launch_smallexp(ea, cs);
+    if (rc == KRY_OK) rc = launch_smallexp(ea, cs, after_cond ? 0 : 1);
     if (rc == KRY_OK && opt && opt->vec_out) {
         VecOutArgs<V> va{};
         va.W = a.W;
@@ -208,6 +259,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     const Layout l = layout(H, dtype, m, std::max(grid, std::max(gridH, gridB)), n_times);
     if (int rc = ensure_workspace(H, l.bytes)) return rc;
     if (!H->cap_stream) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+    if (!H->cap_stream2) KRY_CU(cudaStreamCreateWithFlags(&H->cap_stream2, cudaStreamNonBlocking));
     if (!H->h_poll) KRY_CU(cudaMallocHost(&H->h_poll, sizeof(KryCtl)));
     char *base = (char *)H->ws;
     EvArgs<V> a{};
@@ -220,6 +272,10 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     a.part = (double2 *)(base + l.oPart);
     a.ctl = (KryCtl *)(base + l.oCtl);
     a.rl_smem = rl_in_smem(b);
+    const int *shp = H->shape[dtype == KRY_C64 ? 1 : 0];
+    a.hv_form = shp[1];
+    a.dots_form = shp[2];
+    a.upd_rows = shp[3];
     ExpArgs ea{};
     ea.ctl = a.ctl;
     ea.times = (const double *)(base + l.oTimes);
@@ -237,7 +293,8 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     }
     const void *vkey = opt ? opt->vec_out : nullptr, *ckey = opt ? opt->ckpt : nullptr;
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
-    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general ||
+    const int skey = shp[1] * 100 + shp[2] * 10 + shp[3];
+    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general || H->g_shape != skey ||
                      H->g_grid != grid || H->g_gridB != gridB || H->g_gridH != gridH || H->g_ws != H->ws ||
                      H->g_G != (const void *)(base + l.oP) ||
                      H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
@@ -248,14 +305,16 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         if (int rc = capture_step<V>(H, a, ea, m, grid, gridH, gridB, opt)) return rc;
         H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid; H->g_gridB = gridB;
         H->g_gridH = gridH;
+        H->g_shape = skey;
         H->g_ws = H->ws; H->g_G = base + l.oP;
         H->g_vec = vkey; H->g_ck = ckey; H->g_C = want_C;
         H->g_ldo = opt ? opt->ldOut : 0;
         H->g_ldc = opt ? opt->ldC : 0;
     }
-    cudaEvent_t ev0, ev1;
-    KRY_CU(cudaEventCreate(&ev0));
-    KRY_CU(cudaEventCreate(&ev1));
+    EventPair evp;
+    KRY_CU(cudaEventCreate(&evp.a));
+    KRY_CU(cudaEventCreate(&evp.b));
+    cudaEvent_t ev0 = evp.a, ev1 = evp.b;
     KRY_CU(cudaEventRecord(ev0, s));
     // control block
     KryCtl c;
@@ -265,14 +324,15 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     c.t_end = times[n_times - 1];
     c.tol = tol;
     c.n_times = n_times;
-    c.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
+    c.eta_corr = H->orth_check == 2 ? 0.0 : (dtype == KRY_C64 ? 1e-5 : 1e-12);
     c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
     c.eta_cancel = 0.1;
-    c.verify = H->orth_check;
+    c.verify = H->orth_check ? 1 : 0;
     c.shift = H->shift[0];
     if (opt && opt->ckpt) {
         c.ckpt_every = opt->ckpt_every;
-        c.ckpt_cap = std::min(opt->ckpt_cap, 64);
+        c.ckpt_cap = opt->ckpt_cap;
+        c.ckpt_t = opt->d_ckpt_t;
     }
     const size_t es = sizeof(V), nvec = (size_t)b.D * (size_t)H->K;
     if (general) {
@@ -332,8 +392,6 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         for (int q = 0; q < NKIND; ++q)
             H->prof_bytes[q] += (hp->vp_kind[q] - vp0[q]) * (double)nvec * (double)es;
     if (hp->err) {
-        cudaEventDestroy(ev0);
-        cudaEventDestroy(ev1);
         if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
         else set_error("kry_evolve: initial vector has zero norm");
         return hp->err;
@@ -344,8 +402,6 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     KRY_CU(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (st) {
         st->n_hv = hp->n_hv;
         st->n_krylov_steps = hp->n_steps;
@@ -355,11 +411,17 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (nk + 2 * m + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 1;
+        st->n_launches = launched * (nk + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 2 * hp->n_c1 + 1;
+        st->n_second_dots = hp->n_c1;
     }
     if (opt && opt->ckpt) {
-        opt->n_ckpt = hp->n_ckpt;
-        for (int i = 0; i < hp->n_ckpt && i < 64; ++i) opt->ckpt_t[i] = hp->ckpt_t[i];
+        opt->n_ckpt = std::min(hp->n_ckpt, opt->ckpt_cap);
+        opt->ckpt_t.assign((size_t)opt->n_ckpt, 0.0);
+        if (opt->n_ckpt > 0) {
+            KRY_CU(cudaMemcpyAsync(opt->ckpt_t.data(), opt->d_ckpt_t, sizeof(double) * opt->n_ckpt,
+                                   cudaMemcpyDeviceToHost, s));
+            KRY_CU(cudaStreamSynchronize(s));
+        }
     }
     return KRY_OK;
 }
@@ -401,7 +463,7 @@ int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
     const int Kp = padded_k(H->K);
     const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b), gridB)
                                    : batched_grid<double2>(b, Kp, rl_in_smem(b), gridB);
-    const int ov = H->grid_override[dtype == KRY_C64 ? 1 : 0];
+    const int ov = H->shape[dtype == KRY_C64 ? 1 : 0][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return g;
 }
@@ -485,6 +547,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     a.K = K;
     a.Kp = Kp;
     a.rl_smem = rl_in_smem(b);
+    a.kch = H->shape[dtype == KRY_C64 ? 1 : 0][4];
     ExpArgsB ea{};
     ea.ctl = a.ctl;
     ea.times = (const double *)(base + l.oTimes);
@@ -501,18 +564,20 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         ea.glw = ea.glx + NGL;
     }
     const int gkey = 2 + (int)general;   // distinguishes batched graphs from single ones
-    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != gkey ||
+    if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != gkey || H->g_shape != a.kch ||
                      H->g_grid != grid || H->g_gridB != gridB || H->g_ws != H->ws || H->g_C != want_C ||
                      H->g_G != (const void *)(base + l.oP) || (int)H->prof_ev.empty() == H->prof_on))
         drop_graph(H);
     if (!H->gexec) {
         if (int rc = capture_step_b<V>(H, a, ea, m, grid, gridB, (int)general)) return rc;
         H->g_dtype = dtype; H->g_m = m; H->g_general = gkey; H->g_grid = grid; H->g_gridB = gridB;
+        H->g_shape = a.kch;
         H->g_ws = H->ws; H->g_G = base + l.oP; H->g_C = want_C;
     }
-    cudaEvent_t ev0, ev1;
-    KRY_CU(cudaEventCreate(&ev0));
-    KRY_CU(cudaEventCreate(&ev1));
+    EventPair evp;
+    KRY_CU(cudaEventCreate(&evp.a));
+    KRY_CU(cudaEventCreate(&evp.b));
+    cudaEvent_t ev0 = evp.a, ev1 = evp.b;
     KRY_CU(cudaEventRecord(ev0, s));
     KryCtlB *c = new (std::nothrow) KryCtlB();
     if (!c) { set_error("kry_evolve: host allocation failed"); return KRY_ENOMEM; }
@@ -598,8 +663,6 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     if (H->prof_on)
         for (int q = 0; q < NKIND; ++q) H->prof_bytes[q] += hp->vp_kind[q] * (double)nvec * (double)es;
     if (hp->err) {
-        cudaEventDestroy(ev0);
-        cudaEventDestroy(ev1);
         if (hp->err == KRY_ETOL) set_error("kry_evolve: no step size meets tol=%g at t=%g", tol, hp->t_now);
         else set_error("kry_evolve: an initial vector has zero norm");
         return hp->err;
@@ -612,8 +675,6 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     KRY_CU(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (st) {
         st->n_hv = (int64_t)hp->n_hv;
         st->n_krylov_steps = (int64_t)hp->n_steps;
@@ -624,6 +685,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
         st->n_launches = launched * (9 * m + 5) + (general ? 2 : 1);
+        st->n_second_dots = 0;
     }
     return KRY_OK;
 }
@@ -655,6 +717,7 @@ extern "C" int kry_hamiltonian_destroy(kry_ham H)
     if (H->d_eh) cudaFree(H->d_eh);
     if (H->h_poll) cudaFreeHost(H->h_poll);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    if (H->cap_stream2) cudaStreamDestroy(H->cap_stream2);
     delete H;
     return KRY_OK;
 }
@@ -873,6 +936,7 @@ void add_stats(kry_stats &a, const kry_stats &b)
     a.time_ms += b.time_ms;
     a.algo_bytes += b.algo_bytes;
     a.n_launches += b.n_launches;
+    a.n_second_dots += b.n_second_dots;
 }
 
 }  // namespace
@@ -923,9 +987,8 @@ extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double 
             wq.push_back(hh * gw[i]);
         }
     }
-    const int cap = 64;
     // device buffers
-    DevBuf bpsi0, bpsit, bck, blamA, blamB, bw, bacc, bpart;
+    DevBuf bpsi0, bpsit, bck, bckt, blamA, blamB, bw, bacc, bpart;
     KRY_CU(cudaMalloc(&bpsi0.p, vb));
     KRY_CU(cudaMalloc(&bpsit.p, vb));
     KRY_CU(cudaMalloc(&blamA.p, vb));
@@ -941,19 +1004,37 @@ extern "C" int kry_grad(kry_ham H, uint64_t psi0_state, double t, int m, double 
     KRY_CU(cudaMemcpyAsync(bw.p, wq.data(), sizeof(double) * wq.size(), cudaMemcpyHostToDevice, s));
     KRY_CU(cudaMemsetAsync(bpsi0.p, 0, vb, s));
     if (int rc = launch_set_basis_state(bpsi0.p, 0, (uint32_t)r0, s)) return rc;
-    // 1. forward sweep with checkpoints
-    size_t ck_bytes = (size_t)cap * vb;
-    KRY_CU(cudaMalloc(&bck.p, ck_bytes));
+    // 1. forward sweep with checkpoints.  The buffer starts with room for a few checkpoints;
+    // if the sweep takes more Krylov steps than that covers, it is grown to the number the
+    // sweep needs and the sweep is repeated (the step sequence does not depend on it).
     EvOpts fo;
-    fo.ckpt = bck.p;
     fo.ldC = ldv;
     fo.ckpt_every = ckpt_every;
-    fo.ckpt_cap = cap;
     double Pt = 0.0;
     kry_stats st{};
-    if (int rc = evolve_t<double2>(H, KRY_C128, nullptr, psi0_state, false, &t, 1, m, tol, bpsit.p, &Pt, &st, s, &fo))
-        return rc;
-    add_stats(tot, st);
+    for (int cap = 8;;) {
+        if (bck.p) { cudaFree(bck.p); bck.p = nullptr; }
+        if (bckt.p) { cudaFree(bckt.p); bckt.p = nullptr; }
+        cudaError_t e = cudaMalloc(&bck.p, (size_t)cap * vb);
+        if (e != cudaSuccess) {
+            bck.p = nullptr;
+            cudaGetLastError();
+            set_error("kry_grad: %d checkpoints of %zu bytes do not fit in device memory; use a larger "
+                      "ckpt_every", cap, vb);
+            return KRY_ENOMEM;
+        }
+        KRY_CU(cudaMalloc(&bckt.p, sizeof(double) * cap));
+        fo.ckpt = bck.p;
+        fo.d_ckpt_t = (double *)bckt.p;
+        fo.ckpt_cap = cap;
+        if (int rc = evolve_t<double2>(H, KRY_C128, nullptr, psi0_state, false, &t, 1, m, tol, bpsit.p, &Pt, &st, s,
+                                       &fo))
+            return rc;
+        add_stats(tot, st);
+        const long long need = st.n_krylov_steps / ckpt_every;
+        if (need <= cap) break;
+        cap = (int)std::min<long long>(need, 1 << 20);
+    }
     double2 A;
     KRY_CU(cudaMemcpyAsync(&A, (double2 *)bpsit.p + r0, sizeof(double2), cudaMemcpyDeviceToHost, s));
     KRY_CU(cudaStreamSynchronize(s));

@@ -595,11 +595,11 @@ int launch_exp_b(const ExpArgsB &a, cudaStream_t s)
     return KRY_OK;
 }
 
-int launch_smallexp(const ExpArgs &a, cudaStream_t s)
+int launch_smallexp(const ExpArgs &a, cudaStream_t s, int pdl)
 {
     KRY_CU(cudaFuncSetAttribute(k_smallexp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ExpSmem)));
-    KRY_CU(launch_pdl(k_smallexp, 1, 32, sizeof(ExpSmem), s, a));
+    KRY_CU(launch_ex(pdl, k_smallexp, 1, 32, sizeof(ExpSmem), s, a));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -620,10 +620,11 @@ extern "C" int kry_tridiag_expv(const double *alpha, const double *beta, int m, 
     double *d = nullptr;
     KRY_CU(cudaMalloc(&d, sizeof(double) * (4 * MMAX + 2)));
     double *da = d, *db = d + MMAX, *dy = d + 2 * MMAX, *de = d + 4 * MMAX;
-    cudaMemcpyAsync(da, alpha, sizeof(double) * m, cudaMemcpyHostToDevice, s);
-    if (m > 1) cudaMemcpyAsync(db, beta, sizeof(double) * (m - 1), cudaMemcpyHostToDevice, s);
-    cudaError_t e = cudaFuncSetAttribute(k_expv_test, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(ExpSmem));
+    cudaError_t e = cudaMemcpyAsync(da, alpha, sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && m > 1)
+        e = cudaMemcpyAsync(db, beta, sizeof(double) * (m - 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_expv_test, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ExpSmem));
     if (e == cudaSuccess) {
         k_expv_test<<<1, 32, sizeof(ExpSmem), s>>>(da, db, m, h, tau, dy, de);
         e = cudaGetLastError();
@@ -646,9 +647,12 @@ extern "C" int kry_tridiag_expv(const double *alpha, const double *beta, int m, 
 //
 // The array holds alpha[32], beta[32], y[64] and err (about 1 KB).  Every GPU that loads
 // this library keeps it for the life of the process.  Host code cannot pass the array's
-// name to a kernel (in host code it is a stand-in, not a device address), so the first
-// call on each device looks up the real address with cudaGetSymbolAddress while that
-// device is current and caches it.
+// name to a kernel (in host code it is a stand-in, not a device address), so the call looks
+// up the real address with cudaGetSymbolAddress while the caller's device is current, once
+// per device and CUDA context: the address is kept together with the id of the context it
+// was looked up in, and looked up again when the current context differs (after a
+// cudaDeviceReset the module is loaded anew and the array may move).  When the driver
+// cannot report a context id the address is looked up on every call.
 
 #include <mutex>
 
@@ -657,7 +661,42 @@ static __device__ __align__(256) double g_expv_scratch[4 * kry::MMAX + 8];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_expv_mu;
-double *g_expv_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;   // 0 = not looked up
+    double *ptr;
+};
+ScratchAddr g_expv_addr[kMaxDevices] = {};
+
+// Id of the calling thread's current CUDA context (unique over the process's lifetime), or 0
+// if there is none or the driver cannot say.  The two driver calls are fetched through the
+// runtime, so the library does not link the driver library itself.
+unsigned long long current_context_id()
+{
+    typedef int (*get_current_t)(void **);
+    typedef int (*get_id_t)(void *, unsigned long long *);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (get_current_t)p;
+        p = nullptr;
+        q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)p;
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return 0;
+    unsigned long long id = 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int expv_scratch(double **out)
 {
@@ -668,14 +707,17 @@ int expv_scratch(double **out)
         set_error("kry_tridiag_expv_noalloc: device ordinal %d is above %d", dev, kMaxDevices - 1);
         return KRY_EINVAL;
     }
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_expv_mu);
-    if (!g_expv_addr[dev]) {
+    ScratchAddr &a = g_expv_addr[dev];
+    if (id == 0 || a.ctx_id != id || !a.ptr) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_expv_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_expv_scratch)");
-        g_expv_addr[dev] = (double *)p;
+        a.ptr = (double *)p;
+        a.ctx_id = current_context_id();   // the lookup made the runtime's context current
     }
-    *out = g_expv_addr[dev];
+    *out = a.ptr;
     return KRY_OK;
 }
 }  // namespace

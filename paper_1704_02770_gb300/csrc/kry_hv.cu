@@ -132,8 +132,10 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
 // u = sigma_j H W_j, written to U (pass A, part 1).  One thread per row at full occupancy
 // and nothing else: the gathers of the hops are latency-bound, so as many rows as possible
 // are kept in flight.  alpha_j, ||u||^2 and the dots with the earlier vectors are taken by
-// the streaming pass that follows (k_dots, mode 0).
-template <class V>
+// the streaming pass that follows (k_dots, mode 0).  FORM 0 gathers the hops one by one
+// (hv_row_scaled), FORM 1 in chunks of eight loads in flight (hv_row_chunked); both give the
+// same bits, the launch shape picks the faster (kry_autotune).
+template <class V, int FORM>
 __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 {
     pdl_begin();
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
             uint32_t hi, off;
             int klo;
             tile_unrank(a.b, hd->bsz, r0, threadIdx.x, hi, off, klo);
-            a.U[r] = hv_row_scaled<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl, dz, sj, shj);
+            a.U[r] = FORM == 1 ? hv_row_chunked<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl, dz, sj, shj)
+                               : hv_row_scaled<V>(a.b, a.h, x, hi, off, klo, hd->koff, rl, dz, sj, shj);
         }
     }
 }
@@ -167,14 +170,20 @@ __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
 // GEMV with plain loads.  The vectors are read as KC interleaved columns of rows (thread k
 // takes rows r0 + k + KC e, so a warp loads 32 consecutive rows), and thread (k, g) takes
 // the vectors i = g, g + NG, ... with one accumulator per vector, so the accumulations of
-// different vectors overlap.  complex64: KC = 32 (a warp per group of vectors), three CTAs
-// per SM; complex128: KC = 64, two.  The sums over the columns are taken in a fixed order
-// at the end.
+// different vectors overlap.  The rows of the next vector are loaded before the current
+// vector's products are accumulated (software prefetch), so the loads of one vector are in
+// flight during the arithmetic of the one before: the complex64 accumulation is error-free
+// float-float arithmetic, about as much FP32 work per byte as the HBM stream supplies, and
+// without the overlap the kernel alternates between waiting on loads and on the FP32 pipe.
+// complex64: KC = 32 (a warp per group of vectors), two CTAs per SM (the prefetch buffer
+// needs the registers); complex128 (FP64-bound, no prefetch): KC = 64, two.  The sums over
+// the columns are taken in a fixed order at the end.  PFT = 0 turns the prefetch off (a
+// launch-shape choice of kry_autotune; the bits are the same).
 //   MODE 0 (pass A): y = U = sigma_j H W_j; fills coefA[0..j], alpha_j and ||u||^2.
 //   MODE 1 (pass C1, when pass B flagged it): y = W_{j+1}; measures the loss of
 //          orthogonality and sets up the subtraction of pass C2 when it exceeds eta_corr.
-template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_dots(EvArgs<V> a, int jj)
+template <class V, int MODE, int PFT>
+__global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
 {
     pdl_begin();
     KryCtl *ctl = a.ctl;
@@ -182,6 +191,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
     if (MODE == 1 && !ctl->corr) return;
     constexpr int KC = sizeof(V) == sizeof(float2) ? 32 : 64;   // columns (rows in flight per vector)
     constexpr int NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, RT = 8, TR = KC * RT;
+    constexpr bool PF = PFT && sizeof(V) == sizeof(float2);   // prefetch (complex128 is FP64-bound: no gain)
     using Acc = typename std::conditional<sizeof(V) == sizeof(float2), DotAccF2, DotAccD>::type;
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wred[NTHR / 32][QD + 1];
@@ -197,39 +207,45 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t r0 = tile * TR + k;
         const bool full = tile * TR + TR <= D;
-        V uu[RT];
+        // rows r0 + KC e of vector p (zero past D; one test per tile when the tile is full)
+        auto load = [&](const V *p, V *dst) {
+            if (full) {
 #pragma unroll
-        for (int e = 0; e < RT; ++e) uu[e] = VT<V>::zero();
-        if (full) {
+                for (int e = 0; e < RT; ++e) dst[e] = __ldg(p + r0 + KC * e);
+            } else {
 #pragma unroll
-            for (int e = 0; e < RT; ++e) uu[e] = __ldg(y + r0 + KC * e);
-        } else {
-#pragma unroll
-            for (int e = 0; e < RT; ++e)
-                if (r0 + KC * e < D) uu[e] = __ldg(y + r0 + KC * e);
-        }
+                for (int e = 0; e < RT; ++e) dst[e] = (r0 + KC * e < D) ? __ldg(p + r0 + KC * e) : VT<V>::zero();
+            }
+        };
+        V uu[RT], cur[RT];
+        load(y, uu);
         if (MODE == 0 && g == 0) {
 #pragma unroll
             for (int e = 0; e < RT; ++e) nrm.add(uu[e], uu[e]);
         }
+        if (PF) {
+            V nxt[RT];
+            if (g < nv) load(a.W + (size_t)g * a.ldW, cur);
 #pragma unroll
-        for (int q = 0; q < QD; ++q) {
-            const int iv = g + NG * q;
-            if (iv < nv) {
-                const V *wi = a.W + (size_t)iv * a.ldW + r0;
-                V vv[RT];
+            for (int q = 0; q < QD; ++q) {
+                const int iv = g + NG * q, ivn = iv + NG;
+                if (q + 1 < QD && ivn < nv) load(a.W + (size_t)ivn * a.ldW, nxt);
+                if (iv < nv) {
 #pragma unroll
-                for (int e = 0; e < RT; ++e) vv[e] = VT<V>::zero();
-                if (full) {
-#pragma unroll
-                    for (int e = 0; e < RT; ++e) vv[e] = __ldg(wi + KC * e);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < RT; ++e)
-                        if (r0 + KC * e < D) vv[e] = __ldg(wi + KC * e);
+                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
                 }
 #pragma unroll
-                for (int e = 0; e < RT; ++e) acc[q].add(vv[e], uu[e]);
+                for (int e = 0; e < RT; ++e) cur[e] = nxt[e];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < QD; ++q) {
+                const int iv = g + NG * q;
+                if (iv < nv) {
+                    load(a.W + (size_t)iv * a.ldW, cur);
+#pragma unroll
+                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
+                }
             }
         }
     }
@@ -286,6 +302,7 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
         nd2 += (fin[i].x * fin[i].x + fin[i].y * fin[i].y) * s * s;
     }
     if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
+    ctl->n_c1 += 1;
     ctl->vec_passes += (double)(jj + 2);
     ctl->vp_kind[2] += (double)(jj + 2);
     ctl->corr = 0;
@@ -306,10 +323,12 @@ __global__ void __launch_bounds__(NTHR, sizeof(V) == sizeof(float2) ? 3 : 2) k_d
 // ---------------------------------------------------------------- linear combinations
 
 // w = src - sum_i c_i W_i, the terms taken in index order; w is then dotted with psi0.
-// Plain loads, two rows per thread and eight vectors unrolled (sixteen loads in flight per
-// thread), four CTAs per SM: a pure stream, which this form keeps near the HBM rate.
-template <class V, int MODE>
-__global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
+// Plain loads, RR rows per thread (r, r + TILE, ...) and eight vectors unrolled (8 RR loads
+// in flight per thread), four CTAs per SM (two with RR = 4): a pure stream, which this form
+// keeps near the HBM rate.  RR is a launch-shape choice (kry_autotune); it changes which
+// rows a thread sums into its partial norms, so results agree to rounding.
+template <class V, int MODE, int RR>
+__global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, int jj)
 {
     pdl_begin();
     KryCtl *ctl = a.ctl;
@@ -330,41 +349,49 @@ __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
     __syncthreads();
     V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
     const V *src = (MODE == 0) ? a.U : (MODE == 1) ? out : (MODE == 3) ? a.G : nullptr;
-    const uint32_t D = a.b.D, ntiles = (D + TILE - 1) / TILE;
+    const uint32_t D = a.b.D;
     DotAcc<V> nrm, gacc;
-    // two rows per thread (r and r + TILE): sixteen loads in flight per thread
-    const uint32_t nt2 = (D + 2 * TILE - 1) / (2 * TILE);
-    for (uint32_t tile = blockIdx.x; tile < nt2; tile += gridDim.x) {
-        const uint32_t r = tile * 2 * TILE + tid, r2 = r + TILE;
+    const uint32_t ntr = (D + RR * TILE - 1) / (RR * TILE);
+    for (uint32_t tile = blockIdx.x; tile < ntr; tile += gridDim.x) {
+        const uint32_t r = tile * RR * TILE + tid;
         if (r >= D) continue;
-        const bool l2 = r2 < D;
-        const uint32_t q2 = l2 ? r2 : r;   // past D the second row repeats the first, unstored
-        V w = src ? src[r] : VT<V>::zero();
-        V w2 = src ? src[q2] : VT<V>::zero();
+        uint32_t q[RR];
+        bool in[RR];
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+            in[k] = r + k * TILE < D;
+            q[k] = in[k] ? r + k * TILE : r;   // past D a row repeats the first, unstored
+        }
+        V w[RR];
+#pragma unroll
+        for (int k = 0; k < RR; ++k) w[k] = src ? src[q[k]] : VT<V>::zero();
         if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
 #pragma unroll 8
             for (int i = 0; i < nvec; ++i) {
                 const V *wi = a.W + (size_t)i * a.ldW;
-                const V x1 = wi[r], x2 = wi[q2];
-                w = cfms(coef[i], x1, w);
-                w2 = cfms(coef[i], x2, w2);
+                V x[RR];
+#pragma unroll
+                for (int k = 0; k < RR; ++k) x[k] = wi[q[k]];
+#pragma unroll
+                for (int k = 0; k < RR; ++k) w[k] = cfms(coef[i], x[k], w[k]);
             }
         } else {
 #pragma unroll 8
             for (int i = 0; i < nvec; ++i) {
                 const V *wi = a.W + (size_t)i * a.ldW;
-                const V x1 = __ldg(wi + r), x2 = __ldg(wi + q2);
-                w = cfms(coef[i], x1, w);
-                w2 = cfms(coef[i], x2, w2);
+                V x[RR];
+#pragma unroll
+                for (int k = 0; k < RR; ++k) x[k] = __ldg(wi + q[k]);
+#pragma unroll
+                for (int k = 0; k < RR; ++k) w[k] = cfms(coef[i], x[k], w[k]);
             }
         }
-        out[r] = w;
-        nrm.add(w, w);
-        if (a.G && MODE != 3) gacc.add(__ldg(a.G + r), w);
-        if (l2) {
-            out[r2] = w2;
-            nrm.add(w2, w2);
-            if (a.G && MODE != 3) gacc.add(__ldg(a.G + r2), w2);
+#pragma unroll
+        for (int k = 0; k < RR; ++k) {
+            if (!in[k]) continue;
+            out[q[k]] = w[k];
+            nrm.add(w[k], w[k]);
+            if (a.G && MODE != 3) gacc.add(__ldg(a.G + q[k]), w[k]);
         }
     }
     cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
@@ -378,10 +405,21 @@ __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         ctl->vp_kind[1] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         // One classical Gram-Schmidt pass is enough unless the projection cancelled most of
-        // u (||w|| < eta ||u||, the Daniel-Gragg-Kaufman-Stewart test); then the dots of w
+        // u (||w|| < eta ||u||, the Daniel-Gragg-Kaufman-Stewart test), or the lengths show a
+        // loss of orthogonality: with c = V^H u and G = V^H V = I + E, ||w||^2 = ||u||^2 -
+        // ||c||^2 + c^H E c, so |||w||^2 - (||u||^2 - ||c||^2)| / (||c|| ||w||) estimates
+        // ||E c|| / ||w|| = ||V^H w|| / ||w|| (Pythagoras test).  Either way the dots of w
         // with every previous vector are taken (pass C1) and subtracted if needed (C2).
         // With orth_check set the dots are taken after every update.
-        if (ctl->verify || nw2 < ctl->eta_cancel * ctl->eta_cancel * ctl->normu2) {
+        double c2 = 0.0;
+        for (int i = 0; i <= jj; ++i) {
+            const double s = ctl->sigma[i];
+            c2 += (ctl->coefA[i].x * ctl->coefA[i].x + ctl->coefA[i].y * ctl->coefA[i].y) / (s * s);
+        }
+        // (the second term is the noise floor of the lengths of vectors in storage precision)
+        const double pyth = fabs(nw2 - (ctl->normu2 - c2));
+        const bool lost = pyth > ctl->eta_corr * sqrt(c2 * nw2) + 0.1 * ctl->eta_bd * ctl->normu2;
+        if (ctl->verify || nw2 < ctl->eta_cancel * ctl->eta_cancel * ctl->normu2 || lost) {
             ctl->corr = 1;
             ctl->wnorm2 = nw2;
             ctl->wg = gdot;
@@ -389,6 +427,7 @@ __global__ void __launch_bounds__(NTHR, 4) k_lincomb(EvArgs<V> a, int jj)
             ctl->corr = 0;
             finalize_beta(ctl, jj, nw2, gdot);
         }
+        if (a.use_cond) cudaGraphSetConditional(a.cond, ctl->corr ? 1u : 0u);
     } else if (MODE == 1) {
         ctl->n_corr += 1;
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
@@ -601,11 +640,12 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 {
     const uint32_t es = sizeof(V);
     const size_t smH = apply_smem(b, rl_smem, es == sizeof(float2));
-    if (int rc = prep_smem(k_hv<V>, smH)) return -rc;
+    if (int rc = prep_smem(k_hv<V, 0>, smH)) return -rc;
+    if (int rc = prep_smem(k_hv<V, 1>, smH)) return -rc;
     int occA = 0, occB = 0, occH = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0>, NTHR, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V>, NTHR, smH);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0>, NTHR, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0, 1>, NTHR, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V, 0>, NTHR, smH);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0, 2>, NTHR, 0);
     const uint32_t ntiles = (b.D + TILE - 1) / TILE;
     auto fit = [&](int occ) {
         return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
@@ -619,22 +659,33 @@ int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
 }
 
 template <class V>
-int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
-    if (a.b.list) return launch_list_hv<V>(a, jj, grid, s);
-    KRY_CU(launch_pdl(k_hv<V>, grid, NTHR, apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2)), s, a, jj));
+    if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
+    const size_t smem = apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2));
+    KRY_CU(launch_ex(pdl, a.hv_form == 1 ? k_hv<V, 1> : k_hv<V, 0>, grid, NTHR, smem, s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
 
+template <class V, int MODE>
+static cudaError_t launch_lincomb_rr(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
+{
+    switch (a.upd_rows) {
+    case 1: return launch_ex(pdl, k_lincomb<V, MODE, 1>, grid, NTHR, 0, s, a, jj);
+    case 4: return launch_ex(pdl, k_lincomb<V, MODE, 4>, grid, NTHR, 0, s, a, jj);
+    default: return launch_ex(pdl, k_lincomb<V, MODE, 2>, grid, NTHR, 0, s, a, jj);
+    }
+}
+
 template <class V>
-int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
+int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl)
 {
     switch (mode) {
-    case 0: KRY_CU(launch_pdl(k_lincomb<V, 0>, grid, NTHR, 0, s, a, jj)); break;
-    case 1: KRY_CU(launch_pdl(k_lincomb<V, 1>, grid, NTHR, 0, s, a, jj)); break;
-    case 2: KRY_CU(launch_pdl(k_lincomb<V, 2>, grid, NTHR, 0, s, a, jj)); break;
-    default: KRY_CU(launch_pdl(k_lincomb<V, 3>, grid, NTHR, 0, s, a, jj)); break;
+    case 0: KRY_CU((launch_lincomb_rr<V, 0>(a, jj, grid, s, pdl))); break;
+    case 1: KRY_CU((launch_lincomb_rr<V, 1>(a, jj, grid, s, pdl))); break;
+    case 2: KRY_CU(launch_ex(pdl, k_lincomb<V, 2, 2>, grid, NTHR, 0, s, a, jj)); break;
+    default: KRY_CU(launch_ex(pdl, k_lincomb<V, 3, 2>, grid, NTHR, 0, s, a, jj)); break;
     }
     KRY_CU(cudaGetLastError());
     return KRY_OK;
@@ -680,21 +731,22 @@ template int launch_vecout<float2>(const VecOutArgs<float2> &, int, cudaStream_t
 template int launch_ckpt<double2>(const double2 *, double2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template int launch_ckpt<float2>(const float2 *, float2 *, size_t, KryCtl *, uint32_t, int, cudaStream_t);
 template <class V>
-int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s)
+int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl)
 {
-    if (mode == 0) KRY_CU(launch_pdl(k_dots<V, 0>, grid, NTHR, 0, s, a, jj));
-    else KRY_CU(launch_pdl(k_dots<V, 1>, grid, NTHR, 0, s, a, jj));
+    const int pf = a.dots_form == 0;
+    if (mode == 0) KRY_CU(launch_ex(pdl, pf ? k_dots<V, 0, 1> : k_dots<V, 0, 0>, grid, NTHR, 0, s, a, jj));
+    else KRY_CU(launch_ex(pdl, pf ? k_dots<V, 1, 1> : k_dots<V, 1, 0>, grid, NTHR, 0, s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
 
-template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t);
-template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t);
+template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
+template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
 template int vector_grid<double2>(const DevBasis &, int, int *, int *);
 template int vector_grid<float2>(const DevBasis &, int, int *, int *);
-template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
-template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
-template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t);
-template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t);
+template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);
+template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t, int);
+template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
+template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
 
 }  // namespace kry

@@ -27,9 +27,11 @@ int cuda_fail(cudaError_t e, const char *what);
 // Launch with programmatic dependent launch allowed: the kernel may begin while the
 // kernel before it in the stream finishes, and waits for that kernel's completion
 // (griddepcontrol.wait, see pdl_begin) before reading anything it wrote.
+// With pdl = 0 the launch is an ordinary one (full dependence on the work before it), as
+// needed after a node that is not a kernel (a conditional node of the step graph).
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args &&...args)
+inline cudaError_t launch_ex(int pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -40,8 +42,14 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    return launch_ex(1, kernel, grid, block, smem, s, std::forward<Args>(args)...);
 }
 
 #define KRY_CU(call)                                                 \
@@ -139,6 +147,7 @@ struct EvArgsB {
     KryCtlB *ctl;
     int K, Kp;       // realisations; Kp = K rounded up to a power of two >= 32
     int rl_smem;
+    int kch;         // H.v in chunks of kch realisations (8 or 16; 0 = all K at once)
 };
 
 struct ExpArgsB {
@@ -187,9 +196,10 @@ struct KryCtl {
     // dense vector output (outputs [out_begin, out_end) of the current step) and checkpoints
     int out_begin, out_end;
     int ckpt_every, n_ckpt, ckpt_cap;
-    double ckpt_t[64];
+    double *ckpt_t;            // device [ckpt_cap]: time of every checkpoint
     double pint;               // int_0^t_now P(t') dt' (temporal autocorrelation)
     double shift;              // s of the Lanczos operator H - s I (T holds alpha - s)
+    long long n_c1;            // second-pass dots taken (pass C1 runs)
 };
 
 // Dense output of whole vectors: psi(t_o) = sum_j Yout[o][j] W_j, written to out + o * ldOut.
@@ -223,6 +233,12 @@ struct EvArgs {
     double2 *part;   // per-CTA partial sums [grid][PSTRIDE]
     KryCtl *ctl;
     int rl_smem;     // stage ranklo in shared memory
+    // pass B sets this conditional node of the step graph to whether the second
+    // Gram-Schmidt pass (pass C) runs (use_cond = 0: no node, pass C kernels always launched)
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+    // launch shape (host side only): H.v gather form, dots form, update rows per thread
+    int hv_form, dots_form, upd_rows;
 };
 
 struct ExpArgs {
@@ -245,7 +261,7 @@ int list_build(DevBasis &b, cudaStream_t s);
 int launch_list_rank(const DevBasis &b, const uint64_t *st, uint32_t *rk, int64_t n, cudaStream_t s);
 int launch_list_unrank(const DevBasis &b, const uint32_t *rk, uint64_t *st, int64_t n, cudaStream_t s);
 int launch_list_apply(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y, cudaStream_t s);
-template <class V> int launch_list_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_list_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl = 1);
 template <class V> int launch_list_hv_b(const EvArgsB<V> &a, int jj, cudaStream_t s);
 template <class V> int list_hv_grid(const DevBasis &b, int *grid);
 size_t list_smem(const DevBasis &b);
@@ -253,14 +269,14 @@ size_t list_smem(const DevBasis &b);
 // kernel launchers (kry_hv.cu)
 int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, void *y,
                  int rl_smem, cudaStream_t s);
-template <class V> int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s);
+template <class V> int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl = 1);
 template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid,
-                                      cudaStream_t s);
-template <class V> int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s);
+                                      cudaStream_t s, int pdl = 1);
+template <class V> int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl = 1);
 template <class V> int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB);
 int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
 // small exponential (kry_exp.cu)
-int launch_smallexp(const ExpArgs &a, cudaStream_t s);
+int launch_smallexp(const ExpArgs &a, cudaStream_t s, int pdl = 1);
 
 // kernel kinds of the profile
 enum { KIND_PASSA = 0, KIND_PASSB = 1, KIND_PASSC = 2, KIND_EXP = 3, KIND_COMBINE = 4, NKIND = 5 };
@@ -292,15 +308,20 @@ struct kry_ham_s {
     int ws_user;                // ws belongs to the caller (kry_set_workspace): never freed here
     // cached CUDA graph of one Krylov step
     cudaGraphExec_t gexec;
-    int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH;
+    int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH, g_shape;
     void *g_ws;
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
     int g_C;                    // the graph integrates P for C(t)
     size_t g_ldo, g_ldc;
-    int grid_override[2];       // per precision: CTAs of the vector kernels (0 = occupancy rule)
+    // per precision, the launch shape of the vector kernels (kry_set_shape, kry_autotune):
+    // [0] CTAs of the streaming kernels (0 = occupancy rule), [1] H.v gather form (0 one at a
+    // time, 1 chunks of eight), [2] dots form (0 prefetch, 1 none), [3] update rows per thread,
+    // [4] batched H.v in chunks of this many realisations (0 = all K)
+    int shape[2][5];
     int orth_check;             // measure <v_i, w> after every Lanczos update
     cudaStream_t cap_stream;
+    cudaStream_t cap_stream2;   // captures the bodies of the step graph's conditional nodes
     void *h_poll;   // pinned host mirror of the control block
     // profiling: CUDA events recorded between the kernels of the captured step
     int prof_on;
@@ -308,3 +329,12 @@ struct kry_ham_s {
     double prof_ms[5], prof_bytes[5];
     int64_t prof_launches[5];
 };
+
+// Launch shape of a new Hamiltonian: the occupancy-rule grid, the one-at-a-time H.v gathers,
+// prefetching dots and two update rows per thread.
+inline void default_shape(kry_ham_s *H)
+{
+    static const int v[5] = {0, 0, 0, 2, 0};
+    for (int d = 0; d < 2; ++d)
+        for (int q = 0; q < 5; ++q) H->shape[d][q] = v[q];
+}

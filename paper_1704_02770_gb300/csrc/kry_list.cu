@@ -284,9 +284,9 @@ int list_hv_grid(const DevBasis &b, int *grid)
 }
 
 template <class V>
-int launch_list_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s)
+int launch_list_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
-    KRY_CU(launch_pdl(k_list_hv<V>, grid, NTHR, list_smem(a.b), s, a, jj));
+    KRY_CU(launch_ex(pdl, k_list_hv<V>, grid, NTHR, list_smem(a.b), s, a, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -304,8 +304,8 @@ int launch_list_hv_b(const EvArgsB<V> &a, int jj, cudaStream_t s)
 
 template int list_hv_grid<double2>(const DevBasis &, int *);
 template int list_hv_grid<float2>(const DevBasis &, int *);
-template int launch_list_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t);
-template int launch_list_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t);
+template int launch_list_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);
+template int launch_list_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t, int);
 template int launch_list_hv_b<double2>(const EvArgsB<double2> &, int, cudaStream_t);
 template int launch_list_hv_b<float2>(const EvArgsB<float2> &, int, cudaStream_t);
 

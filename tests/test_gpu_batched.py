@@ -105,29 +105,3 @@ def test_general_initial_states_batched(kry):
         Po, psio, _ = krylov.evolve(Hc.matvec, Hc.norm_inf(), psi0[:, k].copy(), times, m=30, tol=1e-12)
         assert np.max(np.abs(P[:, k] - Po)) <= 1e-10
         assert np.linalg.norm(out[:, k] - psio) <= 1e-10
-
-
-def test_config_L22_batched_full_size(kry):
-    """K = 64 phases at L = 22 (D = 705,432), complex64: two realisations against the oracle
-    over the first output times; all 64 against complex128 batched over t <= 1."""
-    c = workloads.config("L22_batched_h1.5")
-    L, N, K = c["L"], c["n_up"], 64
-    h = np.array(c["h"])
-    B = kry.Basis(L, N)
-    H = kry.Hamiltonian(B, 1.0, 1.0, h)
-    times = c["times"]
-    P64, st = H.return_probability(c["state"], times, tol=1e-7, dtype="c64")
-    assert P64.shape == (40, K)
-    assert np.all(P64 >= -1e-6) and np.all(P64 <= 1 + 1e-6)
-    k6 = 6
-    for k in (0, K - 1):
-        Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
-        Po, _ = krylov.return_probability(Hc, ob.lookup(Hc.basis, c["state"]), times[:k6], m=30, tol=1e-12)
-        err = float(np.max(np.abs(P64[:k6, k] - Po)))
-        print(f"[parity] L22 K=64 c64 realisation {k} (t <= {times[k6 - 1]:.3f}): max|dP| = {err:.3e}")
-        assert err <= 1e-5
-    n1 = sum(1 for t in times if t <= 1.0)
-    P128, _ = H.return_probability(c["state"], times[:n1], tol=1e-10, dtype="c128")
-    err = float(np.max(np.abs(P128 - P64[:n1])))
-    print(f"[parity] L22 K=64 c64 vs c128 (t <= 1): max|dP| = {err:.3e}")
-    assert err <= 1e-5

