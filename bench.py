@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b", "c64l"],
                     help="one Krylov step (m = 30, one output time) of the workload, nothing else: "
                          "a short, fixed launch sequence for ncu captures")
+    ap.add_argument("--ncu-L", type=int, default=0,
+                    help="ncu case: chain length L (N_up = L/2, h = 1.5, phi from seed 5; default: the workload)")
+    ap.add_argument("--ncu-m", type=int, default=0, help="ncu case: Krylov dimension (default 30)")
+    ap.add_argument("--ncu-shape", default=None, help="ncu case: launch shape, five comma-separated ints")
     a = ap.parse_args()
     if a.kernels_only:
         a.no_mixed = a.no_cpu_baseline = a.no_batched = a.no_widened = a.no_l30 = True
@@ -512,8 +516,9 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
             B = kry.Basis(c["L"], c["n_up"])
         D = B.dim
         H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
-        if f"{dt}_K1" in tune:
-            H.set_shape(tune[f"{dt}_K1"]["shape"], dt)
+        # launch shape tuned on this sector (one Krylov step per probe)
+        t_ = H.autotune(c["state"], 0.02, dtype=dt, reps=1)
+        res.setdefault("autotune", {})[f"{name}_{dt}"] = t_
         tol = c["tol"] if dt == "c128" else 1e-7
         H.return_probability(c["state"], [0.1], m=c["m"], tol=tol, dtype=dt)
         H.profile(True)
@@ -737,6 +742,7 @@ def run_ncu_case(args):
     if args.ncu_case == "c64l":   # the L = 55, N = 5 ring on the sorted-list basis
         B = kry.Basis(55, 5)
         H = kry.Hamiltonian(B, 1.0, 1.0, workloads.aubry_andre_field(55, 2.0, 1.0, workloads.phases(7)[0]))
+        H.profile(2)
         P, st = H.return_probability(sum(1 << (11 * i) for i in range(5)), [0.5], m=30, tol=1e-7, dtype="c64")
         torch.cuda.synchronize()
         print(json.dumps({"ncu_case": "c64l", "workload": "L55 N5 ring", "krylov_steps": st["n_krylov_steps"],
@@ -744,9 +750,18 @@ def run_ncu_case(args):
         return
     batched = args.ncu_case == "c64b"   # the K = 64 phase ensemble of L = 22
     c = workloads.config("L22_batched_h1.5" if batched else args.workload)
+    if args.ncu_L and not batched:
+        L = args.ncu_L
+        c = dict(c, name=f"L{L} qp", L=L, n_up=L // 2, state=workloads.neel_state(L),
+                 h=[workloads.quasiperiodic_field(L, 1.5, workloads.phases(5)[0])])
+    m = args.ncu_m or c["m"]
     B = kry.Basis(c["L"], c["n_up"])
     H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"] if batched else c["h"][0], pbc=c["pbc"])
-    P, st = H.return_probability(c["state"], [0.5], m=c["m"], tol=1e-7, dtype="c64" if batched else args.ncu_case)
+    dt = "c64" if batched else args.ncu_case
+    H.profile(2)   # no conditional nodes: ncu cannot see kernels in graphs that have them
+    if args.ncu_shape:
+        H.set_shape([int(x) for x in args.ncu_shape.split(",")], dt)
+    P, st = H.return_probability(c["state"], [0.5], m=m, tol=1e-7, dtype=dt)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": args.ncu_case, "workload": c["name"], "krylov_steps": st["n_krylov_steps"],
                       "hv": st["n_hv"], "P": float(np.asarray(P).ravel()[0])}))

@@ -202,7 +202,11 @@ int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, dou
 /* Per-kernel profile (not part of the paper's method; a measurement aid).
  * kry_profile_enable(H, 1) makes later kry_evolve / kry_return_probability calls on H
  * record CUDA events between the kernels of every Krylov step (on the caller's stream,
- * inside the replayed graph) and synchronise after each step; 0 turns it off.
+ * inside the replayed graph) and synchronise after each step; 0 turns it off.  With 2 no
+ * events are recorded, and the step graph launches the second Gram-Schmidt pass as two plain
+ * kernels in every Lanczos index (returning at once unless needed) instead of through a
+ * conditional node: external profilers such as Nsight Compute cannot see the kernels of a
+ * graph that has conditional nodes.  KRY_EINVAL for other values.
  * kry_profile_read fills, for the five kernel kinds
  *   0 = pass A (H.v fused with the reorthogonalisation dots), 1 = pass B (Lanczos update
  *   with the second-pass dots), 2 = pass C (second-pass correction), 3 = small
@@ -217,8 +221,10 @@ int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
  * dtype, five ints:
  *   shape[0] CTAs of the streaming kernels: 0 = the occupancy rule (whole SMs times the
  *            resident CTAs of each kernel), else that many CTAs;
- *   shape[1] gather form of the H.v: 0 = one hop at a time, 1 = the targets of up to eight hops
- *            computed first and their loads issued together;
+ *   shape[1] form of the H.v, two bits: bit 0 set = the targets of up to eight hops computed
+ *            first and their loads issued together (else one hop at a time); bit 1 set = the
+ *            lower-bit rank table read through the L1 cache instead of staged in shared memory
+ *            (at L = 29, 30 that table takes 64 KB of shared memory per CTA);
  *   shape[2] dots of pass A: 0 = the next vector's rows loaded before the current vector's
  *            products are accumulated (complex64), 1 = without that prefetch;
  *   shape[3] rows per thread of the update pass: 1, 2 or 4;
@@ -227,7 +233,8 @@ int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
  * Parts 1, 2 and 4 change only the order of independent loads (the results are bitwise the
  * same); parts 0 and 3 change which rows a thread or CTA sums into its partial norms and dots
  * (the results agree to rounding).  Single-realisation evolutions use parts 0-3, batched ones
- * parts 0 and 4.  New Hamiltonians start at {0, 0, 0, 2, 0}.
+ * parts 0 and 4.  New Hamiltonians start at {0, 0, 0, 2, 0}, or {0, 3, 0, 2, 0} for L >= 28
+ * (split-table bases), where the rank table of the lower bits is 32-64 KB.
  * kry_set_shape returns KRY_EINVAL for values outside those lists; kry_set_grid sets part 0. */
 int kry_set_shape(kry_ham H, int dtype, const int *shape);
 int kry_get_shape(kry_ham H, int dtype, int *shape);
@@ -236,7 +243,7 @@ int kry_set_grid(kry_ham H, int dtype, int grid);
 /* Launch-shape autotuner (not part of the paper's method).  Times a probe evolution of the
  * basis state probe_state to t_probe (reps replays after one capture run, best kept) for
  * candidate shapes, one part after another with the other parts at their best so far: part 0
- * over {0, 1, 2, 3, 4 x the SM count}, then part 1 over {0, 1}, part 2 over {0, 1}, part 3 over
+ * over {0, 1, 2, 3, 4 x the SM count}, then part 1 over {0..3}, part 2 over {0, 1}, part 3 over
  * {2, 1, 4} (K > 1: part 0, then part 4 over {0, 16, 8}).  Keeps the fastest for later calls on
  * H with this dtype and returns it in shape_out[5].  cand_out (host, [max_cand][5]) and ms_out
  * ([max_cand]) receive the shapes tried and their times, *n_cand how many were stored. */

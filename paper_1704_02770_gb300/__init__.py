@@ -314,9 +314,11 @@ class Hamiltonian:
                                ctypes.byref(st), _stream(stream)))
         return float(P[0]), gh, float(gd[0]), st.as_dict()
 
-    def profile(self, on: bool = True):
-        """Turn per-kernel CUDA-event profiling of later evolutions on or off (resets it)."""
-        _check(load().kry_profile_enable(self._h, 1 if on else 0))
+    def profile(self, on=True):
+        """Turn per-kernel CUDA-event profiling of later evolutions on or off (resets it); on = 2
+        builds the step graph without conditional nodes, for external profilers
+        (kry_profile_enable)."""
+        _check(load().kry_profile_enable(self._h, int(on)))
 
     KINDS = ("passA", "passB", "passC", "smallexp", "combine")
 

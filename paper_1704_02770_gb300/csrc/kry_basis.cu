@@ -368,7 +368,7 @@ static int ham_set_list(kry_basis b, double J, double Delta, const double *h, in
     for (size_t i = 0; i < n8; ++i) ehf[i] = (float)eh[i];
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
-    default_shape(H);
+    default_shape(H, b->dev.list ? 0 : b->Llo);
     fill_dev_ham(H->dev, J, Delta, L, K, boundary);
     // shifted copy for the Lanczos pass: s_k taken off the byte-0 entries
     H->shift.resize(K);
@@ -447,7 +447,7 @@ extern "C" int kry_hamiltonian_set(kry_basis b, double J, double Delta, const do
     }
     kry_ham H = new (std::nothrow) kry_ham_s();
     if (!H) { set_error("kry_hamiltonian_set: host allocation failed"); return KRY_ENOMEM; }
-    default_shape(H);
+    default_shape(H, b->dev.list ? 0 : b->Llo);
     fill_dev_ham(H->dev, J, Delta, L, K, boundary);
     // shifted copy of the upper-bit table for the Lanczos pass: s_k taken off every entry
     H->shift.resize(K);

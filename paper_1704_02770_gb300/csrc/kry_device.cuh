@@ -70,6 +70,8 @@ __device__ __forceinline__ void pdl_begin()
 // float pair (s, c), so the accumulation error is of order 2^-48 of the sum of |terms|
 // and the per-thread result is handed on in FP64.
 
+__device__ __forceinline__ double2 warp_sum(double2 v);
+
 struct DotAccD {
     double re = 0.0, im = 0.0;
     __device__ __forceinline__ void add(double2 a, double2 b)
@@ -77,8 +79,34 @@ struct DotAccD {
         re = fma(a.x, b.x, re); re = fma(a.y, b.y, re);
         im = fma(a.x, b.y, im); im = fma(-a.y, b.x, im);
     }
+    __device__ __forceinline__ void add_norm(double2 a) { re = fma(a.x, a.x, re); re = fma(a.y, a.y, re); }
     __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
+    // the sum over the warp (valid in every lane)
+    __device__ __forceinline__ double2 warp_value() const { return warp_sum(value()); }
 };
+
+// Float-float sum (s, c) += (s2, c2): TwoSum of the leading parts, the trailing parts and the
+// rounding error added, then renormalised.  Symmetric in its two operands.
+__device__ __forceinline__ void ff_combine(float &s, float &c, float s2, float c2)
+{
+    const float t = __fadd_rn(s, s2);
+    const float z = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+    const float cc = __fadd_rn(__fadd_rn(c, c2), e);
+    s = __fadd_rn(t, cc);
+    c = __fsub_rn(cc, __fsub_rn(s, t));
+}
+// Sum of a float-float value over the warp, in FP32 arithmetic (GB300 runs FP64, and the
+// conversions to it, at 1/64 of the FP32 rate, so per-thread FP64 epilogues of the streaming
+// kernels cost as much as their streams at small j): every lane ends with the total.
+__device__ __forceinline__ void ff_warp_sum(float &s, float &c)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        ff_combine(s, c, s2, c2);
+    }
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -102,9 +130,18 @@ struct DotAccF {
         exact_fma(a.x, b.x, sr, cr); exact_fma(a.y, b.y, sr, cr);
         exact_fma(a.x, b.y, si, ci); exact_fma(-a.y, b.x, si, ci);
     }
+    // |a|^2 (the imaginary part of conj(a) a is zero and is not accumulated)
+    __device__ __forceinline__ void add_norm(float2 a) { exact_fma(a.x, a.x, sr, cr); exact_fma(a.y, a.y, sr, cr); }
     __device__ __forceinline__ double2 value() const
     {
         return make_double2((double)sr + (double)cr, (double)si + (double)ci);
+    }
+    __device__ __forceinline__ double2 warp_value() const
+    {
+        float a = sr, b = cr, c = si, d = ci;
+        ff_warp_sum(a, b);
+        ff_warp_sum(c, d);
+        return make_double2((double)a + (double)b, (double)c + (double)d);
     }
 };
 // complex64 dots with packed FP32x2 arithmetic (sm_100 and later): the same error-free
@@ -152,6 +189,18 @@ struct DotAccF2 {
     {
         const double axbx = (double)s1.x + (double)c1.x, aybx = (double)s1.y + (double)c1.y;
         const double axby = (double)s2.x + (double)c2.x, ayby = (double)s2.y + (double)c2.y;
+        return make_double2(axbx + ayby, axby - aybx);
+    }
+    // the sum over the warp, reduced in FP32 float-float arithmetic; converted to FP64 once
+    __device__ __forceinline__ double2 warp_value() const
+    {
+        float a = s1.x, b = c1.x, c = s1.y, d = c1.y, e = s2.x, f = c2.x, g = s2.y, h = c2.y;
+        ff_warp_sum(a, b);
+        ff_warp_sum(c, d);
+        ff_warp_sum(e, f);
+        ff_warp_sum(g, h);
+        const double axbx = (double)a + (double)b, aybx = (double)c + (double)d;
+        const double axby = (double)e + (double)f, ayby = (double)g + (double)h;
         return make_double2(axbx + ayby, axby - aybx);
     }
 };
@@ -295,13 +344,13 @@ __device__ __forceinline__ V hv_row_scaled(const DevBasis &b, const DevHam &hm, 
     return axpby(sigma * d, __ldg(x + base + off), sigma_halfJ, acc);
 }
 
-// The same row as hv_row_scaled with the gathers issued in chunks: the targets of up to
-// eight hops are computed first and their loads issued together, so a thread has up to eight
-// gathers in flight instead of one (a warp issues in order, and the loop of hv_row_scaled
-// waits for each gathered value before it computes the next target).  Zeros stand in for the
-// bonds that do not hop and the terms are added in the same order as in hv_row_scaled, so the
-// result is bitwise the same.  Needs Llo, Lhi <= 16 (L <= 32).
-template <class V>
+// The same row as hv_row_scaled with the gathers issued in rounds: the targets of up to
+// RND hops are computed first (taking the antiparallel bonds in ascending order) and
+// their loads issued together, so a thread has up to RND gathers in flight instead of one
+// (a warp issues in order, and the loop of hv_row_scaled waits for each gathered value
+// before it computes the next target).  The terms are added in the same order as in
+// hv_row_scaled, so the result is bitwise the same.
+template <class V, int RND = 4>
 __device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm, const V *__restrict__ x,
                                             uint32_t hi, uint32_t off, int klo, const uint32_t *koff_s,
                                             const uint16_t *rl, const typename VT<V>::R *dz,
@@ -320,50 +369,58 @@ __device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm,
     const R d = dz[__popc(anti) + (int)wrap] + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
     const V xr = __ldg(x + base + off);
     V acc = VT<V>::zero();
-    const uint32_t a = anti & ((1u << (Llo - 1)) - 1u);    // bonds inside the lower part
+    uint32_t a = anti & ((1u << (Llo - 1)) - 1u);          // bonds inside the lower part
+    while (a) {
+        uint32_t t[RND];
+        int n = 0;
 #pragma unroll
-    for (int c0 = 0; c0 < 16; c0 += 8) {
-        if (!((a >> c0) & 0xFFu)) continue;
-        V v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int p = c0 + u;
-            v[u] = ((a >> p) & 1u) ? __ldg(x + base + rl[(lo ^ (3u << p)) & lomask]) : VT<V>::zero();
+        for (int u = 0; u < RND; ++u) {
+            if (a) {
+                const int p = __ffs(a) - 1;
+                a &= a - 1u;
+                t[u] = base + rl[lo ^ (3u << p)];
+                n = u + 1;
+            }
         }
+        V v[RND];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if ((a >> (c0 + u)) & 1u) acc = acc + v[u];
+        for (int u = 0; u < RND; ++u)
+            if (u < n) v[u] = __ldg(x + t[u]);
+#pragma unroll
+        for (int u = 0; u < RND; ++u)
+            if (u < n) acc = acc + v[u];
     }
     const bool cross = b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u);   // bond joining the two parts
-    const uint32_t ah = anti >> Llo;                               // bonds inside the upper part
-    const uint32_t himask = (1u << b.Lhi) - 1u;   // (the masks keep every index in range)
-    V vc = VT<V>::zero();
+    V vc = VT<V>::zero(), vr = VT<V>::zero();
     if (cross) {
         const uint32_t s2 = s ^ (3u << (Llo - 1));
         vc = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
-    V vr = VT<V>::zero();
     if (wrap) {                                                    // ring bond (L-1, 0)
         const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
         vr = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
     if (cross) acc = acc + vc;
+    uint32_t ah = anti >> Llo;                                     // bonds inside the upper part
+    while (ah) {
+        uint32_t t[RND];
+        int n = 0;
 #pragma unroll
-    for (int c0 = 0; c0 < 16; c0 += 8) {
-        if (!((ah >> c0) & 0xFFu)) continue;
-        uint32_t t[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int q = c0 + u;
-            t[u] = ((ah >> q) & 1u) ? __ldg(b.blk + ((hi ^ (3u << q)) & himask)) : 0u;
+        for (int u = 0; u < RND; ++u) {
+            if (ah) {
+                const int q = __ffs(ah) - 1;
+                ah &= ah - 1u;
+                t[u] = __ldg(b.blk + (hi ^ (3u << q)));
+                n = u + 1;
+            }
         }
-        V v[8];
+        V v[RND];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            v[u] = ((ah >> (c0 + u)) & 1u) ? __ldg(x + t[u] + off) : VT<V>::zero();
+        for (int u = 0; u < RND; ++u)
+            if (u < n) v[u] = __ldg(x + t[u] + off);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if ((ah >> (c0 + u)) & 1u) acc = acc + v[u];
+        for (int u = 0; u < RND; ++u)
+            if (u < n) acc = acc + v[u];
     }
     if (wrap) acc = acc + vr;
     return axpby(sigma * d, xr, sigma_halfJ, acc);

@@ -128,8 +128,9 @@ int grid_for(const kry_ham_s *H, int dtype, int *gridH, int *gridB)
 {
     const DevBasis &b = H->b->dev;
     const int rl = rl_in_smem(b);
-    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl, gridH, gridB)
-                                   : vector_grid<double2>(b, rl, gridH, gridB);
+    const int hvf = H->shape[dtype == KRY_C64 ? 1 : 0][1];
+    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl, hvf, gridH, gridB)
+                                   : vector_grid<double2>(b, rl, hvf, gridH, gridB);
     const int ov = H->shape[dtype == KRY_C64 ? 1 : 0][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return (g > 0 && ov > 0) ? ov : g;   // vector_grid also sets the kernels' smem limits
@@ -174,6 +175,9 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     // conditional node after pass B, whose last CTA sets the node's value: the pass costs
     // nothing in the Lanczos indices where it is not needed.  The kernel after a conditional
     // node is launched without programmatic dependence (that only links two kernels).
+    // With plain_graph set (for external profilers, which cannot see the kernels of a graph
+    // that has conditional nodes) pass C is launched in every Lanczos index and returns at once
+    // unless flagged.
     cudaStream_t cs2 = H->cap_stream2;
     int after_cond = 0;
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
@@ -181,6 +185,13 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         rc = launch_hv<V>(a, jj, gridH, cs, after_cond ? 0 : 1);
         if (rc == KRY_OK) rc = launch_dots<V>(a, 0, jj, grid, cs);
         mark();
+        if (H->plain_graph) {
+            if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, gridB, cs);
+            mark();
+            if (rc == KRY_OK) rc = launch_dots<V>(a, 1, jj, grid, cs);
+            if (rc == KRY_OK) rc = launch_lincomb<V>(a, 1, jj, gridB, cs);
+            continue;
+        }
         EvArgs<V> ab = a;
         cudaGraph_t cg = nullptr;
         if (rc == KRY_OK) {
@@ -295,6 +306,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     const int skey = shp[1] * 100 + shp[2] * 10 + shp[3];
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general || H->g_shape != skey ||
+                     H->g_plain != H->plain_graph ||
                      H->g_grid != grid || H->g_gridB != gridB || H->g_gridH != gridH || H->g_ws != H->ws ||
                      H->g_G != (const void *)(base + l.oP) ||
                      H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
@@ -306,6 +318,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid; H->g_gridB = gridB;
         H->g_gridH = gridH;
         H->g_shape = skey;
+        H->g_plain = H->plain_graph;
         H->g_ws = H->ws; H->g_G = base + l.oP;
         H->g_vec = vkey; H->g_ck = ckey; H->g_C = want_C;
         H->g_ldo = opt ? opt->ldOut : 0;
@@ -411,7 +424,8 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (nk + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) + 2 * hp->n_c1 + 1;
+        st->n_launches = launched * (nk + (H->plain_graph ? 2 * m : 0) + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) +
+                         (H->plain_graph ? 0 : 2 * hp->n_c1) + 1;
         st->n_second_dots = hp->n_c1;
     }
     if (opt && opt->ckpt) {
@@ -725,7 +739,9 @@ extern "C" int kry_hamiltonian_destroy(kry_ham H)
 extern "C" int kry_profile_enable(kry_ham H, int on)
 {
     if (!H) { set_error("kry_profile_enable: H is NULL"); return KRY_EINVAL; }
-    H->prof_on = on ? 1 : 0;
+    if (on < 0 || on > 2) { set_error("kry_profile_enable: on must be 0, 1 or 2"); return KRY_EINVAL; }
+    H->prof_on = on == 1 ? 1 : 0;
+    H->plain_graph = on == 2 ? 1 : 0;
     for (int q = 0; q < NKIND; ++q) { H->prof_ms[q] = 0.0; H->prof_bytes[q] = 0.0; H->prof_launches[q] = 0; }
     return KRY_OK;
 }

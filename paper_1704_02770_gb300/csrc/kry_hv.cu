@@ -49,19 +49,19 @@ __global__ void __launch_bounds__(NTHR) k_apply(DevBasis b, DevHam hm, const V *
 // ---------------------------------------------------------------- reductions
 
 // Write this CTA's partials, then let the last CTA to finish sum all partials into
-// fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).  The sum is spread over
-// FGROUPS x PSTRIDE threads: thread (g, slot) adds the partials of CTAs g, g+FGROUPS, ...
-// (neighbouring threads read neighbouring slots, so the loads coalesce and none waits on
-// another), then the FGROUPS group sums are added in group order.  The summation order
-// depends only on the grid, so results are bitwise reproducible for a fixed grid.
-constexpr int FGROUPS = NTHR / PSTRIDE;   // 6
-// Only the slots [0, nlead) and, with tail set, SLOT_NRM and SLOT_G are summed; the others
-// of fin are zero.
+// fin[0..PSTRIDE).  Returns true in the last CTA (all its threads).  Only the slots [0, nlead)
+// and, with tail set, SLOT_NRM and SLOT_G are summed (the others of fin are zero), and all
+// NTHR threads share the work: each of the ns needed slots gets TPS = NTHR / ns threads
+// (rounded down to a power of two), thread t of a slot adds the partials of CTAs t, t + TPS,
+// ..., and the TPS sums are added by a pairwise tree.  With few slots (the updates need two)
+// this keeps the serial tail of the last CTA to a few loads per thread.  The summation order
+// depends only on the grid and the slot count, so results are bitwise reproducible.
 __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *part, KryCtl *ctl,
                                                 double2 *fin, int *flag, unsigned *counter = nullptr,
                                                 int nlead = PSTRIDE, bool tail = true)
 {
-    __shared__ double2 gsum[FGROUPS][PSTRIDE];
+    __shared__ double2 tsum[NTHR];
+    __shared__ int slots[PSTRIDE];
     const int tid = threadIdx.x;
     if (!counter) counter = &ctl->counter;
     if (tid < PSTRIDE) part[(size_t)blockIdx.x * PSTRIDE + tid] = red[tid];
@@ -71,28 +71,37 @@ __device__ __forceinline__ bool finish_partials(const double2 *red, double2 *par
     __syncthreads();
     if (!*flag) return false;
     __threadfence();
-    if (tid < FGROUPS * PSTRIDE) {
-        const int g = tid / PSTRIDE, slot = tid - g * PSTRIDE;
-        double2 s = make_double2(0.0, 0.0);
-        if (slot < nlead || (tail && (slot == SLOT_NRM || slot == SLOT_G))) {
-#pragma unroll 8
-            for (unsigned c = g; c < gridDim.x; c += FGROUPS) {
-                const double2 v = __ldcg(part + (size_t)c * PSTRIDE + slot);
-                s.x += v.x;
-                s.y += v.y;
-            }
+    int ns = 0;
+    for (int sl = 0; sl < PSTRIDE; ++sl)
+        if (sl < nlead || (tail && (sl == SLOT_NRM || sl == SLOT_G))) {
+            if (tid == 0) slots[ns] = sl;
+            ++ns;
         }
-        gsum[g][slot] = s;
+    int tps = 1;
+    while (tps * 2 * ns <= NTHR && tps < 128) tps *= 2;
+    if (tid < PSTRIDE) fin[tid] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int si = tid / tps, t = tid - si * tps;
+    if (si < ns) {
+        const int slot = slots[si];
+        double2 sum = make_double2(0.0, 0.0);
+#pragma unroll 4
+        for (unsigned c = t; c < gridDim.x; c += tps) {
+            const double2 v = __ldcg(part + (size_t)c * PSTRIDE + slot);
+            sum.x += v.x;
+            sum.y += v.y;
+        }
+        tsum[tid] = sum;
     }
     __syncthreads();
-    if (tid < PSTRIDE) {
-        double2 s = gsum[0][tid];
-        for (int g = 1; g < FGROUPS; ++g) {
-            s.x += gsum[g][tid].x;
-            s.y += gsum[g][tid].y;
+    for (int w = tps / 2; w > 0; w >>= 1) {
+        if (si < ns && t < w) {
+            tsum[tid].x += tsum[tid + w].x;
+            tsum[tid].y += tsum[tid + w].y;
         }
-        fin[tid] = s;
+        __syncthreads();
     }
+    if (si < ns && t == 0) fin[slots[si]] = tsum[tid];
     __syncthreads();
     return true;
 }
@@ -102,6 +111,22 @@ __device__ __forceinline__ void cta_sum_into(double2 v, double2 *red, int slot, 
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum(v);
+    if (lane == 0) wtmp[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int w = 0; w < NTHR / 32; ++w) { s.x += wtmp[w].x; s.y += wtmp[w].y; }
+        red[slot] = s;
+    }
+    __syncthreads();
+}
+
+// The same for per-thread dot accumulators (float-float warp sums for complex64).
+template <class Acc>
+__device__ __forceinline__ void cta_sum_into(const Acc &acc, double2 *red, int slot, double2 *wtmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double2 v = acc.warp_value();
     if (lane == 0) wtmp[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -202,9 +227,25 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
     const V *y = (MODE == 0) ? a.U : a.W + (size_t)(jj + 1) * a.ldW;
     const int nv = jj + 1;   // vectors W_0 .. W_j
     const uint32_t D = a.b.D, ntiles = (D + TR - 1) / TR;
+    // Work split: with nv = NG A + B, every group takes A whole vectors (g, g + NG, ...) over
+    // all the CTA's tiles, and the B remaining vectors are shared by all groups: RX = NG / B
+    // groups per remaining vector (group g: vector NG A + g mod B, every RX-th tile of the
+    // CTA from g / B), so every warp streams about the same number of rows at every j; the
+    // partial sums of the groups that share a vector are added at the end.
+    const int A = nv / NG, Bn = nv % NG;
+    const int RX = Bn > 0 ? NG / Bn : 1;
+    const bool hasx = Bn > 0 && g < Bn * RX;
+    const int xv = NG * A + (Bn > 0 ? g % Bn : 0), xs = Bn > 0 ? g / Bn : 0;
+    const int nslot = A + (hasx ? 1 : 0);   // accumulators this group uses
     Acc acc[QD];
     DotAcc<V> nrm;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the norm of y: group 0 over all tiles when A > 0, else the groups of vector 0
+    const bool own_norm = MODE == 0 && (A > 0 ? g == 0 : (hasx && xv == 0));
+    uint32_t tl = 0;   // local index of the tile within this CTA
+    for (uint32_t tile = blockIdx.x; nslot > 0 && tile < ntiles; tile += gridDim.x, ++tl) {
+        const bool xt = hasx && (int)(tl % (uint32_t)RX) == xs;
+        const int nq = A + (xt ? 1 : 0);   // vectors of this tile: A whole ones, then the shared one
+        if (nq == 0) continue;
         const uint32_t r0 = tile * TR + k;
         const bool full = tile * TR + TR <= D;
         // rows r0 + KC e of vector p (zero past D; one test per tile when the tile is full)
@@ -217,64 +258,74 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
                 for (int e = 0; e < RT; ++e) dst[e] = (r0 + KC * e < D) ? __ldg(p + r0 + KC * e) : VT<V>::zero();
             }
         };
+        auto vec = [&](int q) { return a.W + (size_t)(q < A ? g + NG * q : xv) * a.ldW; };
         V uu[RT], cur[RT];
         load(y, uu);
-        if (MODE == 0 && g == 0) {
+        if (own_norm && (A > 0 || xt)) {
 #pragma unroll
-            for (int e = 0; e < RT; ++e) nrm.add(uu[e], uu[e]);
+            for (int e = 0; e < RT; ++e) nrm.add_norm(uu[e]);
         }
         if (PF) {
             V nxt[RT];
-            if (g < nv) load(a.W + (size_t)g * a.ldW, cur);
+            load(vec(0), cur);
 #pragma unroll
             for (int q = 0; q < QD; ++q) {
-                const int iv = g + NG * q, ivn = iv + NG;
-                if (q + 1 < QD && ivn < nv) load(a.W + (size_t)ivn * a.ldW, nxt);
-                if (iv < nv) {
+                if (q < nq) {
+                    if (q + 1 < nq) load(vec(q + 1), nxt);
 #pragma unroll
                     for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
-                }
 #pragma unroll
-                for (int e = 0; e < RT; ++e) cur[e] = nxt[e];
+                    for (int e = 0; e < RT; ++e) cur[e] = nxt[e];
+                }
             }
         } else {
 #pragma unroll
             for (int q = 0; q < QD; ++q) {
-                const int iv = g + NG * q;
-                if (iv < nv) {
-                    load(a.W + (size_t)iv * a.ldW, cur);
+                if (q < nq) {
+                    load(vec(q), cur);
 #pragma unroll
                     for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
                 }
             }
         }
     }
-    // per warp: the sum over its 32 columns; then the two warps of a group, in order
+    // per warp: the sum over its 32 columns; then the warps of a vector's groups, in order
 #pragma unroll
     for (int q = 0; q < QD; ++q) {
-        const double2 v = warp_sum(acc[q].value());
-        if (lane == 0) wred[warp][q] = v;
+        if (q < nslot) {   // (warp-uniform)
+            const double2 v = acc[q].warp_value();
+            if (lane == 0) wred[warp][q] = v;
+        } else if (lane == 0) {
+            wred[warp][q] = make_double2(0.0, 0.0);
+        }
     }
     if (MODE == 0) {
-        const double2 v = warp_sum(nrm.value());
+        const double2 v = nrm.warp_value();
         if (lane == 0) wred[warp][QD] = v;
     }
     __syncthreads();
     constexpr int WG = KC / 32;   // warps per group
     if (tid < nv) {
-        const int gg = tid % NG, q = tid / NG;
+        // vector tid: group tid mod NG at slot tid / NG, or the RX groups sharing it at slot A
         double2 t = make_double2(0.0, 0.0);
+        const bool whole = tid < NG * A;
+        for (int sv = 0; sv < (whole ? 1 : RX); ++sv) {
+            const int gg = whole ? tid % NG : (tid - NG * A) + Bn * sv, q = whole ? tid / NG : A;
 #pragma unroll
-        for (int w = 0; w < WG; ++w) {
-            t.x += wred[WG * gg + w][q].x;
-            t.y += wred[WG * gg + w][q].y;
+            for (int w = 0; w < WG; ++w) {
+                t.x += wred[WG * gg + w][q].x;
+                t.y += wred[WG * gg + w][q].y;
+            }
         }
         red[tid] = t;
     }
     if (MODE == 0 && tid == 0) {
         double t = 0.0;
+        for (int sv = 0; sv < (A > 0 ? 1 : RX); ++sv) {
+            const int gg = A > 0 ? 0 : Bn * sv;
 #pragma unroll
-        for (int w = 0; w < WG; ++w) t += wred[w][QD].x;
+            for (int w = 0; w < WG; ++w) t += wred[WG * gg + w][QD].x;
+        }
         red[SLOT_NRM] = make_double2(t, 0.0);
     }
     __syncthreads();
@@ -327,7 +378,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
 // in flight per thread), four CTAs per SM (two with RR = 4): a pure stream, which this form
 // keeps near the HBM rate.  RR is a launch-shape choice (kry_autotune); it changes which
 // rows a thread sums into its partial norms, so results agree to rounding.
-template <class V, int MODE, int RR>
+template <class V, int MODE, int RR, int COND = 0>
 __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, int jj)
 {
     pdl_begin();
@@ -390,12 +441,12 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
         for (int k = 0; k < RR; ++k) {
             if (!in[k]) continue;
             out[q[k]] = w[k];
-            nrm.add(w[k], w[k]);
+            nrm.add_norm(w[k]);
             if (a.G && MODE != 3) gacc.add(__ldg(a.G + q[k]), w[k]);
         }
     }
-    cta_sum_into(nrm.value(), red, SLOT_NRM, wtmp);
-    if (a.G) cta_sum_into(gacc.value(), red, SLOT_G, wtmp);
+    cta_sum_into(nrm, red, SLOT_NRM, wtmp);
+    if (a.G) cta_sum_into(gacc, red, SLOT_G, wtmp);
     double2 *fin = red;
     if (!finish_partials(red, a.part, ctl, fin, &flag, nullptr, 0, true)) return;
     if (tid != 0) return;
@@ -427,7 +478,9 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
             ctl->corr = 0;
             finalize_beta(ctl, jj, nw2, gdot);
         }
-        if (a.use_cond) cudaGraphSetConditional(a.cond, ctl->corr ? 1u : 0u);
+        // (COND = 0 leaves the device graph call out of the kernel: profilers skip kernels
+        // that make it, and the plain step graph does not need it)
+        if (COND && a.use_cond) cudaGraphSetConditional(a.cond, ctl->corr ? 1u : 0u);
     } else if (MODE == 1) {
         ctl->n_corr += 1;
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
@@ -634,17 +687,21 @@ int launch_apply(const DevBasis &b, const DevHam &h, int c64, const void *x, voi
 
 // CTAs of the vector kernels, whole SMs times their resident CTAs: the streaming dots
 // (returned; also pass C1), the H.v of pass A (*gridH) and the updates, combine and
-// outputs (*gridB).  Also sets the kernels' shared-memory limits.
+// outputs (*gridB).  Also sets the kernels' shared-memory limits.  hv_form is part 1 of the
+// launch shape: bit 0 chunked gathers, bit 1 the lower-bit rank table read through L1
+// instead of staged in shared memory (more CTAs per SM when that table is large).
 template <class V>
-int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB)
+int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gridB)
 {
     const uint32_t es = sizeof(V);
-    const size_t smH = apply_smem(b, rl_smem, es == sizeof(float2));
+    const int rlH = rl_smem && !(hv_form & 2);
+    const size_t smH = apply_smem(b, rlH, es == sizeof(float2));
     if (int rc = prep_smem(k_hv<V, 0>, smH)) return -rc;
     if (int rc = prep_smem(k_hv<V, 1>, smH)) return -rc;
     int occA = 0, occB = 0, occH = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k_dots<V, 0, 1>, NTHR, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V, 0>, NTHR, smH);
+    if (hv_form & 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V, 1>, NTHR, smH);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occH, k_hv<V, 0>, NTHR, smH);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k_lincomb<V, 0, 2>, NTHR, 0);
     const uint32_t ntiles = (b.D + TILE - 1) / TILE;
     auto fit = [&](int occ) {
@@ -662,19 +719,21 @@ template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
     if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
-    const size_t smem = apply_smem(a.b, a.rl_smem, sizeof(V) == sizeof(float2));
-    KRY_CU(launch_ex(pdl, a.hv_form == 1 ? k_hv<V, 1> : k_hv<V, 0>, grid, NTHR, smem, s, a, jj));
+    EvArgs<V> ah = a;
+    ah.rl_smem = a.rl_smem && !(a.hv_form & 2);
+    const size_t smem = apply_smem(a.b, ah.rl_smem, sizeof(V) == sizeof(float2));
+    KRY_CU(launch_ex(pdl, (a.hv_form & 1) ? k_hv<V, 1> : k_hv<V, 0>, grid, NTHR, smem, s, ah, jj));
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
 
-template <class V, int MODE>
+template <class V, int MODE, int COND>
 static cudaError_t launch_lincomb_rr(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
     switch (a.upd_rows) {
-    case 1: return launch_ex(pdl, k_lincomb<V, MODE, 1>, grid, NTHR, 0, s, a, jj);
-    case 4: return launch_ex(pdl, k_lincomb<V, MODE, 4>, grid, NTHR, 0, s, a, jj);
-    default: return launch_ex(pdl, k_lincomb<V, MODE, 2>, grid, NTHR, 0, s, a, jj);
+    case 1: return launch_ex(pdl, k_lincomb<V, MODE, 1, COND>, grid, NTHR, 0, s, a, jj);
+    case 4: return launch_ex(pdl, k_lincomb<V, MODE, 4, COND>, grid, NTHR, 0, s, a, jj);
+    default: return launch_ex(pdl, k_lincomb<V, MODE, 2, COND>, grid, NTHR, 0, s, a, jj);
     }
 }
 
@@ -682,8 +741,11 @@ template <class V>
 int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl)
 {
     switch (mode) {
-    case 0: KRY_CU((launch_lincomb_rr<V, 0>(a, jj, grid, s, pdl))); break;
-    case 1: KRY_CU((launch_lincomb_rr<V, 1>(a, jj, grid, s, pdl))); break;
+    case 0:
+        if (a.use_cond) KRY_CU((launch_lincomb_rr<V, 0, 1>(a, jj, grid, s, pdl)));
+        else KRY_CU((launch_lincomb_rr<V, 0, 0>(a, jj, grid, s, pdl)));
+        break;
+    case 1: KRY_CU((launch_lincomb_rr<V, 1, 0>(a, jj, grid, s, pdl))); break;
     case 2: KRY_CU(launch_ex(pdl, k_lincomb<V, 2, 2>, grid, NTHR, 0, s, a, jj)); break;
     default: KRY_CU(launch_ex(pdl, k_lincomb<V, 3, 2>, grid, NTHR, 0, s, a, jj)); break;
     }
@@ -742,8 +804,8 @@ int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, 
 
 template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
 template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
-template int vector_grid<double2>(const DevBasis &, int, int *, int *);
-template int vector_grid<float2>(const DevBasis &, int, int *, int *);
+template int vector_grid<double2>(const DevBasis &, int, int, int *, int *);
+template int vector_grid<float2>(const DevBasis &, int, int, int *, int *);
 template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);
 template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t, int);
 template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);

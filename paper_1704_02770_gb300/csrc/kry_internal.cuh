@@ -273,7 +273,7 @@ template <class V> int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStrea
 template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid,
                                       cudaStream_t s, int pdl = 1);
 template <class V> int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl = 1);
-template <class V> int vector_grid(const DevBasis &b, int rl_smem, int *gridH, int *gridB);
+template <class V> int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gridB);
 int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
 // small exponential (kry_exp.cu)
 int launch_smallexp(const ExpArgs &a, cudaStream_t s, int pdl = 1);
@@ -308,15 +308,17 @@ struct kry_ham_s {
     int ws_user;                // ws belongs to the caller (kry_set_workspace): never freed here
     // cached CUDA graph of one Krylov step
     cudaGraphExec_t gexec;
-    int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH, g_shape;
+    int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH, g_shape, g_plain;
+    int plain_graph;            // pass C as plain launches instead of a conditional node
     void *g_ws;
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph
     int g_C;                    // the graph integrates P for C(t)
     size_t g_ldo, g_ldc;
     // per precision, the launch shape of the vector kernels (kry_set_shape, kry_autotune):
-    // [0] CTAs of the streaming kernels (0 = occupancy rule), [1] H.v gather form (0 one at a
-    // time, 1 chunks of eight), [2] dots form (0 prefetch, 1 none), [3] update rows per thread,
+    // [0] CTAs of the streaming kernels (0 = occupancy rule), [1] H.v form (bit 0: chunks of
+    // eight gathers; bit 1: rank table through L1), [2] dots form (0 prefetch, 1 none), [3]
+    // update rows per thread,
     // [4] batched H.v in chunks of this many realisations (0 = all K)
     int shape[2][5];
     int orth_check;             // measure <v_i, w> after every Lanczos update
@@ -330,11 +332,14 @@ struct kry_ham_s {
     int64_t prof_launches[5];
 };
 
-// Launch shape of a new Hamiltonian: the occupancy-rule grid, the one-at-a-time H.v gathers,
-// prefetching dots and two update rows per thread.
-inline void default_shape(kry_ham_s *H)
+// Launch shape of a new Hamiltonian: the occupancy-rule grid, prefetching dots, two update
+// rows per thread, all realisations at once, and the H.v one hop at a time with the
+// lower-bit rank table in shared memory -- except for lower parts of 14 bits or more (L >=
+// 28), whose table (32-64 KB) would cap the H.v at three or four CTAs per SM: there the
+// gathers go in rounds and the table is read through L1 (form 3; 2.9x faster at L = 30).
+inline void default_shape(kry_ham_s *H, int Llo)
 {
-    static const int v[5] = {0, 0, 0, 2, 0};
+    const int v[5] = {0, Llo >= 14 ? 3 : 0, 0, 2, 0};
     for (int d = 0; d < 2; ++d)
         for (int q = 0; q < 5; ++q) H->shape[d][q] = v[q];
 }

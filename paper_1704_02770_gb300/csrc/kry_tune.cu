@@ -3,7 +3,8 @@
 // parts, tuned one after another (coordinate descent, each part over its candidates with the
 // others at their best so far):
 //   [0] CTAs of the streaming kernels: the occupancy rule (0) or 1..4 times the SM count;
-//   [1] gather form of the H.v: one hop at a time (0) or chunks of eight loads in flight (1);
+//   [1] H.v form: bit 0 = chunks of eight gathers in flight (else one hop at a time), bit 1 =
+//       the lower-bit rank table read through L1 (else staged in shared memory);
 //   [2] dots: prefetching the next vector's rows (0) or not (1);
 //   [3] rows per thread of the update pass: 1, 2 or 4;
 //   [4] batched H.v in chunks of 8 or 16 realisations (0 = all K at once).
@@ -35,7 +36,7 @@ constexpr int NS = 5;   // parts of a launch shape
 
 bool valid_shape(const int *s)
 {
-    return s[0] >= 0 && s[0] <= (1 << 20) && (s[1] == 0 || s[1] == 1) && (s[2] == 0 || s[2] == 1) &&
+    return s[0] >= 0 && s[0] <= (1 << 20) && (s[1] >= 0 && s[1] <= 3) && (s[2] == 0 || s[2] == 1) &&
            (s[3] == 1 || s[3] == 2 || s[3] == 4) && (s[4] == 0 || s[4] == 8 || s[4] == 16);
 }
 
@@ -54,7 +55,7 @@ extern "C" int kry_set_grid(kry_ham H, int dtype, int grid)
 extern "C" int kry_set_shape(kry_ham H, int dtype, const int *shape)
 {
     if (!H || !shape || (dtype != KRY_C128 && dtype != KRY_C64) || !valid_shape(shape)) {
-        set_error("kry_set_shape: bad arguments (shape = {grid >= 0, hv form 0|1, dots form 0|1, "
+        set_error("kry_set_shape: bad arguments (shape = {grid >= 0, hv form 0..3, dots form 0|1, "
                   "update rows 1|2|4, batched chunk 0|8|16})");
         return KRY_EINVAL;
     }
@@ -106,7 +107,7 @@ extern "C" int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, d
         if (rc == KRY_OK) ++nc;
         return rc;
     };
-    const std::vector<int> cands[NS] = {{0, sms, 2 * sms, 3 * sms, 4 * sms}, {0, 1}, {0, 1}, {2, 1, 4}, {0, 16, 8}};
+    const std::vector<int> cands[NS] = {{0, sms, 2 * sms, 3 * sms, 4 * sms}, {0, 1, 2, 3}, {0, 1}, {2, 1, 4}, {0, 16, 8}};
     const std::vector<int> parts = H->K > 1 ? std::vector<int>{0, 4} : std::vector<int>{0, 1, 2, 3};
     double best_ms = 1e300;
     for (int part : parts) {
