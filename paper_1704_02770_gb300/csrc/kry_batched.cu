@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
     // float-float pairs while they fit the registers (K <= 64), else with the scalar pairs;
     // complex128 in FP64
     constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG - 1) / NG;
-    constexpr int RH = TROWS / 2;   // rows per half tile
     using Acc = typename std::conditional<sizeof(V) == sizeof(float2) && KQ <= 2, DotAccF2, DotAcc<V>>::type;
+    constexpr int RH = TROWS / 2;   // rows per half tile
     const int tid = threadIdx.x, K = a.K;
     const int k = tid % Kp, g = tid / Kp;
     const uint32_t D = a.b.D, ntiles = (D + TROWS - 1) / TROWS;
@@ -258,24 +258,27 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
                 }
                 if (g == 0) {
 #pragma unroll
-                    for (int rr = 0; rr < RH; ++rr) nrm.add(uu[rr], uu[rr]);
+                    for (int rr = 0; rr < RH; ++rr) nrm.add_norm(uu[rr]);
                 }
+                // rows rh .. rh + RH of vector iv, column k (zero past D)
+                auto load = [&](int iv, V *dst) {
+                    const V *wi = a.W + (size_t)iv * a.ldW + (size_t)rh * K + k;
+                    if (nr == RH) {
+#pragma unroll
+                        for (int rr = 0; rr < RH; ++rr) dst[rr] = __ldg(wi + (size_t)rr * K);
+                    } else {
+#pragma unroll
+                        for (int rr = 0; rr < RH; ++rr) dst[rr] = (rr < nr) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+                    }
+                };
+                // (a prefetch of the next vector's rows, as in the single-realisation dots,
+                // needs more registers than the eight accumulators of K = 64 leave, and spills)
 #pragma unroll
                 for (int q = 0; q < QD; ++q) {
                     const int iv = g + NG * q;
                     if (iv <= jj) {
-                        const V *wi = a.W + (size_t)iv * a.ldW + (size_t)rh * K + k;
                         V vv[RH];
-#pragma unroll
-                        for (int rr = 0; rr < RH; ++rr) vv[rr] = VT<V>::zero();
-                        if (nr == RH) {
-#pragma unroll
-                            for (int rr = 0; rr < RH; ++rr) vv[rr] = __ldg(wi + (size_t)rr * K);
-                        } else {
-#pragma unroll
-                            for (int rr = 0; rr < RH; ++rr)
-                                if (rr < nr) vv[rr] = __ldg(wi + (size_t)rr * K);
-                        }
+                        load(iv, vv);
 #pragma unroll
                         for (int rr = 0; rr < RH; ++rr) acc[q].add(vv[rr], uu[rr]);
                     }
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
     }
     if (g == 0) pc[(size_t)SLOT_NRM * Kp + k] = make_double2(nrm.value().x, 0.0);
 }
+
 
 // ---------------------------------------------------------------- linear combinations (batched)
 
