@@ -50,7 +50,7 @@ def parse():
                     help="precision of the timed region in --kernels-only mode")
     ap.add_argument("--kernels-only", action="store_true",
                     help="FP64 timed region only (no mixed, e2e or CPU legs)")
-    ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b", "c64l"],
+    ap.add_argument("--ncu-case", choices=["c128", "c64", "c64b", "c64l", "c128e"],
                     help="one Krylov step (m = 30, one output time) of the workload, nothing else: "
                          "a short, fixed launch sequence for ncu captures")
     ap.add_argument("--ncu-L", type=int, default=0,

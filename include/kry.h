@@ -51,7 +51,14 @@ enum {
     KRY_ECUDA = 5      /* a CUDA runtime call failed                                    */
 };
 enum { KRY_OBC = 0, KRY_PBC = 1 };
-enum { KRY_C128 = 0, KRY_C64 = 1 };
+/* Element types of the state vectors.  KRY_C128: complex128 with FP64 arithmetic.  KRY_C64:
+ * complex64 vectors and H.v, FP64 Lanczos coefficients and FP64-grade (float-float) dots.
+ * KRY_C128E: complex128 storage (the same vectors as KRY_C128) with the vector arithmetic
+ * (H.v sums, dots, updates) done in float-float on the FP32 pipe, about 47 significant bits,
+ * because GB300 runs FP64 at 1/64 of its FP32 rate; the Lanczos coefficients, the small
+ * exponential and the step control stay FP64.  KRY_C128E serves single-realisation
+ * evolutions (K = 1) on split-table bases (L <= 32); elsewhere it returns KRY_EINVAL. */
+enum { KRY_C128 = 0, KRY_C64 = 1, KRY_C128E = 2 };
 
 /* Counters of one kry_evolve / kry_return_probability call. */
 typedef struct kry_stats {

@@ -14,7 +14,11 @@ LIB_PATH = os.path.join(_HERE, "lib", "libkry_gb300.so")
 
 KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ETOL, KRY_ETIMEOUT, KRY_ECUDA = range(6)
 KRY_OBC, KRY_PBC = 0, 1
-KRY_C128, KRY_C64 = 0, 1
+KRY_C128, KRY_C64, KRY_C128E = 0, 1, 2
+# dtype names: complex128 (FP64 arithmetic), complex64 (mixed precision), and complex128
+# storage with float-float arithmetic on the FP32 pipe
+_CODES = {"c128": KRY_C128, "complex128": KRY_C128, "c64": KRY_C64, "complex64": KRY_C64,
+          "c128e": KRY_C128E}
 MMAX = 32
 
 # Every symbol the header declares, with (restype, argtypes).
@@ -105,10 +109,16 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dtype_code(t):
+def _code(dtype: str) -> int:
+    if dtype not in _CODES:
+        raise ValueError(f"unknown dtype {dtype!r}: use one of {sorted(_CODES)}")
+    return _CODES[dtype]
+
+
+def _dtype_code(t, emulated: bool = False):
     import torch
     if t.dtype == torch.complex128:
-        return KRY_C128
+        return KRY_C128E if emulated else KRY_C128
     if t.dtype == torch.complex64:
         return KRY_C64
     raise TypeError(f"unsupported dtype {t.dtype}: use complex128 or complex64")
@@ -190,13 +200,16 @@ class Hamiltonian:
         _check(load().kry_apply(self._h, _dtype_code(x), _dev_ptr(x, n), _dev_ptr(y, n), _stream(stream)))
         return y
 
-    def evolve(self, psi0, times, m: int = 30, tol: float = 1e-10, psi_out=None, stream=None):
+    def evolve(self, psi0, times, m: int = 30, tol: float = 1e-10, psi_out=None, emulated: bool = False,
+               stream=None):
+        """kry_evolve; a complex128 psi0 runs in FP64, or with `emulated` in float-float on the
+        FP32 pipe (KRY_C128E)."""
         import numpy as np
         t, tp = _host_doubles(times)
         P = np.zeros(t.size * self.K)
         st = Stats()
         n = self.basis.dim * self.K
-        _check(load().kry_evolve(self._h, _dtype_code(psi0), _dev_ptr(psi0, n), tp, t.size, m, tol,
+        _check(load().kry_evolve(self._h, _dtype_code(psi0, emulated), _dev_ptr(psi0, n), tp, t.size, m, tol,
                                  _dev_ptr(psi_out, n) if psi_out is not None else None,
                                  P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
@@ -207,7 +220,7 @@ class Hamiltonian:
         t, tp = _host_doubles(times)
         P = np.zeros(t.size * self.K)
         st = Stats()
-        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        code = _code(dtype)
         _check(load().kry_return_probability(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                              P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
@@ -221,7 +234,7 @@ class Hamiltonian:
         C = np.zeros(t.size * self.K)
         P = np.zeros(t.size * self.K)
         st = Stats()
-        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        code = _code(dtype)
         _check(load().kry_autocorrelation(self._h, code, ctypes.c_uint64(state), tp, t.size, m, tol,
                                           C.ctypes.data_as(_dp), P.ctypes.data_as(_dp), ctypes.byref(st),
                                           _stream(stream)))
@@ -241,7 +254,7 @@ class Hamiltonian:
         P = np.zeros(t.size * self.K)
         C = np.zeros(t.size * self.K) if autocorrelation else None
         st = Stats()
-        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        code = _code(dtype)
         _check(load().kry_return_probability_states(
             self._h, code, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), tp, t.size, m, tol,
             P.ctypes.data_as(_dp), C.ctypes.data_as(_dp) if C is not None else None, ctypes.byref(st),
@@ -258,7 +271,7 @@ class Hamiltonian:
         and GPU is reused instead of measuring, and new results are added to the file."""
         import json
         import torch
-        code = KRY_C64 if dtype in ("c64", "complex64") else KRY_C128
+        code = _code(dtype)
         key = (f"{torch.cuda.get_device_name()}|L{self.basis.L}|N{self.basis.n_up}|K{self.K}|"
                f"{dtype}|m{m}")
         db = {}
@@ -286,11 +299,11 @@ class Hamiltonian:
     def set_shape(self, shape, dtype: str = "c128"):
         """Launch shape [grid, hv form, dots form, update rows, batched chunk] (kry_set_shape)."""
         arr = (ctypes.c_int * 5)(*[int(x) for x in shape])
-        _check(load().kry_set_shape(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, arr))
+        _check(load().kry_set_shape(self._h, _code(dtype), arr))
 
     def get_shape(self, dtype: str = "c128"):
         arr = (ctypes.c_int * 5)()
-        _check(load().kry_get_shape(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, arr))
+        _check(load().kry_get_shape(self._h, _code(dtype), arr))
         return list(arr)
 
     def orth_check(self, on=True):
@@ -299,7 +312,7 @@ class Hamiltonian:
         _check(load().kry_set_orth_check(self._h, int(on)))
 
     def set_grid(self, grid: int, dtype: str = "c128"):
-        _check(load().kry_set_grid(self._h, KRY_C64 if dtype in ("c64", "complex64") else KRY_C128, grid))
+        _check(load().kry_set_grid(self._h, _code(dtype), grid))
 
     def grad(self, state: int, t: float, m: int = 30, tol: float = 1e-10, ckpt_every: int = 8,
              stream=None):
@@ -331,7 +344,7 @@ class Hamiltonian:
                 for i, k in enumerate(self.KINDS)}
 
     def workspace_size(self, dtype: str = "c128", m: int = 30, n_times: int = 1) -> int:
-        return int(load().kry_workspace_bytes(self._h, KRY_C64 if dtype == "c64" else KRY_C128, m, n_times))
+        return int(load().kry_workspace_bytes(self._h, _code(dtype), m, n_times))
 
     def set_workspace(self, buf=None):
         """Use a caller-owned device buffer (a CUDA tensor, kept referenced here) as the evolution

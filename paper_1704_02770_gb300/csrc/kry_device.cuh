@@ -26,6 +26,91 @@ template <> struct VT<float2> {
     __device__ __forceinline__ static float2 from(double2 c) { return make_float2((float)c.x, (float)c.y); }
 };
 
+// ---------------------------------------------------------------- FP64 storage, FP32-pipe arithmetic
+// GB300 runs FP64 arithmetic, and conversions between FP64 and FP32, at 1/64 of its FP32
+// rate, so the complex128 passes are bound by the FP64 pipe at about a third of the HBM rate.
+// The element type dd2 (kry_internal.cuh) keeps the vectors in FP64 (the layout of double2)
+// and does the vector arithmetic on the FP32 pipe: every double is split by integer operations on its bits into
+// hi + lo floats (its leading 24 significant bits and the next 23, both truncated), products
+// are formed exactly for the hi parts (the fused multiply-add error term) with the cross
+// terms in float, and sums are float-float (Knuth's TwoSum).  The arithmetic carries about 47
+// significant bits (relative error of a dot product about 2^-47 of the sum of |terms|, where
+// FP64 gives 2^-53); each result is rounded back to FP64 with one FP64 add.
+// hi + lo floats of x (|x| in [2^-80, 2^128); smaller magnitudes give 0, which for vectors of
+// norm of order one changes a dot product by less than 2^-80 D^(1/2))
+__device__ __forceinline__ float2 dsplit(double x)
+{
+    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const unsigned ex = (hw >> 20) & 0x7ffu;
+    const bool ok = ex >= 943u && ex <= 1150u;
+    const unsigned sg = hw & 0x80000000u;
+    const float hi = __uint_as_float(ok ? (sg | ((ex - 896u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29)) : 0u);
+    const float lm = __fsub_rn(__uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)), 8388608.0f);   // exact
+    const float sc = __uint_as_float(ok ? (sg | ((ex - 942u) << 23)) : 0u);                            // +-2^(e-46)
+    return make_float2(hi, __fmul_rn(lm, sc));
+}
+__device__ __forceinline__ void ff_combine(float &s, float &c, float s2, float c2);
+
+// a float as a double, exactly, by integer operations (zero and subnormal floats give 0)
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+    const unsigned hi = e ? ((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)) : 0u;
+    const unsigned lo = e ? ((b & 7u) << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+// float-float s + c rounded to FP64 (one FP64 add)
+__device__ __forceinline__ double ff2d(float s, float c) { return f2d(s) + f2d(c); }
+// (s, c) += (ah + al)(bh + bl): the hi product split exactly (TwoSum into s), the error term and
+// the cross terms into c
+__device__ __forceinline__ void ff_mac(float ah, float al, float bh, float bl, float &s, float &c)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+template <> struct VT<dd2> {
+    using R = double;
+    __device__ __forceinline__ static dd2 zero() { return dd2{0.0, 0.0}; }
+    __device__ __forceinline__ static double ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_d + p); }
+    __device__ __forceinline__ static double ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_d + p); }
+    __device__ __forceinline__ static double eh8(const DevHam &h, size_t p) { return __ldg(h.eh8_d + p); }
+    __device__ __forceinline__ static dd2 from(double2 c) { return dd2{c.x, c.y}; }
+};
+__device__ __forceinline__ dd2 ldg(const dd2 *p)
+{
+    const double2 v = __ldg((const double2 *)p);
+    return dd2{v.x, v.y};
+}
+__device__ __forceinline__ float2 ldg(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg(const double2 *p) { return __ldg(p); }
+
+// Per element type: the accumulator of a neighbour sum (HvSum), of a linear combination (Lin),
+// a coefficient as kept in shared memory (Coef), a right-hand vector element prepared for
+// several dot products (Pre).  For complex64 and complex128 these are the element itself.
+struct FF4 {   // two float-float numbers (real, imaginary)
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+};
+template <class V> struct Arith {
+    using HvSum = V;
+    using Lin = V;
+    using Coef = V;
+    using Pre = V;
+};
+template <> struct Arith<dd2> {
+    using HvSum = FF4;
+    using Lin = FF4;
+    using Coef = float4;   // (re hi, re lo, im hi, im lo)
+    using Pre = float4;
+};
+
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
@@ -48,6 +133,64 @@ __device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a)
 {
     return make_float2(fmaf(d, x.x, s * a.x), fmaf(d, x.y, s * a.y));
 }
+// neighbour sums of the H.v row: acc += v, then y = sd x + shj acc
+template <class V> __device__ __forceinline__ void hv_add(V &acc, V v) { acc = acc + v; }
+__device__ __forceinline__ void hv_add(FF4 &acc, dd2 v)
+{
+    const float2 a = dsplit(v.x), b = dsplit(v.y);
+    ff_combine(acc.sr, acc.cr, a.x, a.y);
+    ff_combine(acc.si, acc.ci, b.x, b.y);
+}
+__device__ __forceinline__ double2 axpby(double d, double2 x, double s, double2 a);
+__device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a);
+template <class V, class R> __device__ __forceinline__ V hv_finish(R sd, V x, R shj, V acc) { return axpby(sd, x, shj, acc); }
+__device__ __forceinline__ dd2 hv_finish(double sd, dd2 x, double shj, const FF4 &acc)
+{
+    const float2 d = dsplit(sd), h = dsplit(shj), xr = dsplit(x.x), xi = dsplit(x.y);
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    ff_mac(d.x, d.y, xr.x, xr.y, sr, cr);
+    ff_mac(h.x, h.y, acc.sr, acc.cr, sr, cr);
+    ff_mac(d.x, d.y, xi.x, xi.y, si, ci);
+    ff_mac(h.x, h.y, acc.si, acc.ci, si, ci);
+    return dd2{ff2d(sr, cr), ff2d(si, ci)};
+}
+// linear combinations: w = src - sum_i c_i x_i
+template <class V> __device__ __forceinline__ V lin_init(V src) { return src; }
+template <class V> __device__ __forceinline__ V lin_out(V w) { return w; }
+template <class V> __device__ __forceinline__ typename Arith<V>::Coef coef_from(double2 c) { return VT<V>::from(c); }
+__device__ __forceinline__ FF4 lin_init(dd2 src)
+{
+    const float2 a = dsplit(src.x), b = dsplit(src.y);
+    FF4 w;
+    w.sr = a.x; w.cr = a.y; w.si = b.x; w.ci = b.y;
+    return w;
+}
+__device__ __forceinline__ dd2 lin_out(const FF4 &w) { return dd2{ff2d(w.sr, w.cr), ff2d(w.si, w.ci)}; }
+template <> __device__ __forceinline__ float4 coef_from<dd2>(double2 c)
+{
+    const float2 a = dsplit(c.x), b = dsplit(c.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ double2 cfms(double2 c, double2 v, double2 w);
+__device__ __forceinline__ float2 cfms(float2 c, float2 v, float2 w);
+template <class V> __device__ __forceinline__ void lin_fms(V &w, V c, V x) { w = cfms(c, x, w); }
+__device__ __forceinline__ void lin_fms(FF4 &w, float4 c, dd2 x)
+{
+    // w -= c x: re -= cr xr - ci xi, im -= cr xi + ci xr
+    const float2 xr = dsplit(x.x), xi = dsplit(x.y);
+    ff_mac(-c.x, -c.y, xr.x, xr.y, w.sr, w.cr);
+    ff_mac(c.z, c.w, xi.x, xi.y, w.sr, w.cr);
+    ff_mac(-c.x, -c.y, xi.x, xi.y, w.si, w.ci);
+    ff_mac(-c.z, -c.w, xr.x, xr.y, w.si, w.ci);
+}
+// a right-hand vector element prepared for several dot products
+template <class V> __device__ __forceinline__ V pre(V u) { return u; }
+__device__ __forceinline__ float4 pre(dd2 u)
+{
+    const float2 a = dsplit(u.x), b = dsplit(u.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 __device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
 __device__ __forceinline__ float2 scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
@@ -205,9 +348,39 @@ struct DotAccF2 {
     }
 };
 
+// sum conj(a) b for FP64-stored vectors in float-float arithmetic (dd2)
+struct DotAccDD {
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    // b prepared by pre(): (bx hi, bx lo, by hi, by lo)
+    __device__ __forceinline__ void add(dd2 a, float4 b)
+    {
+        const float2 ax = dsplit(a.x), ay = dsplit(a.y);
+        ff_mac(ax.x, ax.y, b.x, b.y, sr, cr);
+        ff_mac(ay.x, ay.y, b.z, b.w, sr, cr);
+        ff_mac(ax.x, ax.y, b.z, b.w, si, ci);
+        ff_mac(-ay.x, -ay.y, b.x, b.y, si, ci);
+    }
+    __device__ __forceinline__ void add(dd2 a, dd2 b) { add(a, pre(b)); }
+    __device__ __forceinline__ void add_norm(dd2 a)
+    {
+        const float2 ax = dsplit(a.x), ay = dsplit(a.y);
+        ff_mac(ax.x, ax.y, ax.x, ax.y, sr, cr);
+        ff_mac(ay.x, ay.y, ay.x, ay.y, sr, cr);
+    }
+    __device__ __forceinline__ double2 value() const { return make_double2(ff2d(sr, cr), ff2d(si, ci)); }
+    __device__ __forceinline__ double2 warp_value() const
+    {
+        float a = sr, b = cr, c = si, d = ci;
+        ff_warp_sum(a, b);
+        ff_warp_sum(c, d);
+        return make_double2(ff2d(a, b), ff2d(c, d));
+    }
+};
+
 template <class V> struct DotAcc;
 template <> struct DotAcc<double2> : DotAccD {};
 template <> struct DotAcc<float2> : DotAccF {};
+template <> struct DotAcc<dd2> : DotAccDD {};
 
 __device__ __forceinline__ double2 warp_sum(double2 v)
 {
@@ -320,28 +493,28 @@ __device__ __forceinline__ V hv_row_scaled(const DevBasis &b, const DevHam &hm, 
     const uint32_t anti = (s ^ (s >> 1)) & obc;
     const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
     const R d = dz[__popc(anti) + (int)wrap] + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
-    V acc = VT<V>::zero();
+    typename Arith<V>::HvSum acc{};
     uint32_t a = anti & ((1u << (Llo - 1)) - 1u);          // bonds inside the lower part
     while (a) {
         const int p = __ffs(a) - 1;
         a &= a - 1u;
-        acc = acc + __ldg(x + base + rl[lo ^ (3u << p)]);
+        hv_add(acc, ldg(x + base + rl[lo ^ (3u << p)]));
     }
     if (b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u)) {         // bond joining the two parts
         const uint32_t s2 = s ^ (3u << (Llo - 1));
-        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+        hv_add(acc, ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]));
     }
     uint32_t ah = anti >> Llo;                              // bonds inside the upper part
     while (ah) {
         const int q = __ffs(ah) - 1;
         ah &= ah - 1u;
-        acc = acc + __ldg(x + __ldg(b.blk + (hi ^ (3u << q))) + off);
+        hv_add(acc, ldg(x + __ldg(b.blk + (hi ^ (3u << q))) + off));
     }
     if (wrap) {                                             // ring bond (L-1, 0)
         const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
-        acc = acc + __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+        hv_add(acc, ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]));
     }
-    return axpby(sigma * d, __ldg(x + base + off), sigma_halfJ, acc);
+    return hv_finish(sigma * d, ldg(x + base + off), sigma_halfJ, acc);
 }
 
 // The same row as hv_row_scaled with the gathers issued in rounds: the targets of up to
@@ -367,8 +540,8 @@ __device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm,
     const uint32_t anti = (s ^ (s >> 1)) & obc;
     const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
     const R d = dz[__popc(anti) + (int)wrap] + VT<V>::ehlo(hm, pos) + VT<V>::ehhi(hm, hi);
-    const V xr = __ldg(x + base + off);
-    V acc = VT<V>::zero();
+    const V xr = ldg(x + base + off);
+    typename Arith<V>::HvSum acc{};
     uint32_t a = anti & ((1u << (Llo - 1)) - 1u);          // bonds inside the lower part
     while (a) {
         uint32_t t[RND];
@@ -385,22 +558,22 @@ __device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm,
         V v[RND];
 #pragma unroll
         for (int u = 0; u < RND; ++u)
-            if (u < n) v[u] = __ldg(x + t[u]);
+            if (u < n) v[u] = ldg(x + t[u]);
 #pragma unroll
         for (int u = 0; u < RND; ++u)
-            if (u < n) acc = acc + v[u];
+            if (u < n) hv_add(acc, v[u]);
     }
     const bool cross = b.Lhi > 0 && ((anti >> (Llo - 1)) & 1u);   // bond joining the two parts
     V vc = VT<V>::zero(), vr = VT<V>::zero();
     if (cross) {
         const uint32_t s2 = s ^ (3u << (Llo - 1));
-        vc = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+        vc = ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
     if (wrap) {                                                    // ring bond (L-1, 0)
         const uint32_t s2 = s ^ ((1u << (L - 1)) | 1u);
-        vr = __ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
+        vr = ldg(x + __ldg(b.blk + (s2 >> Llo)) + rl[s2 & lomask]);
     }
-    if (cross) acc = acc + vc;
+    if (cross) hv_add(acc, vc);
     uint32_t ah = anti >> Llo;                                     // bonds inside the upper part
     while (ah) {
         uint32_t t[RND];
@@ -417,13 +590,13 @@ __device__ __forceinline__ V hv_row_chunked(const DevBasis &b, const DevHam &hm,
         V v[RND];
 #pragma unroll
         for (int u = 0; u < RND; ++u)
-            if (u < n) v[u] = __ldg(x + t[u] + off);
+            if (u < n) v[u] = ldg(x + t[u] + off);
 #pragma unroll
         for (int u = 0; u < RND; ++u)
-            if (u < n) acc = acc + v[u];
+            if (u < n) hv_add(acc, v[u]);
     }
-    if (wrap) acc = acc + vr;
-    return axpby(sigma * d, xr, sigma_halfJ, acc);
+    if (wrap) hv_add(acc, vr);
+    return hv_finish(sigma * d, xr, sigma_halfJ, acc);
 }
 
 }  // namespace kry

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "kry_internal.cuh"
 
@@ -30,7 +31,7 @@ uint64_t binom_host(int n, int k)
     return r;
 }
 
-size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(double2); }
+size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(double2); }   // (dd2 = double2)
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -128,10 +129,11 @@ int grid_for(const kry_ham_s *H, int dtype, int *gridH, int *gridB)
 {
     const DevBasis &b = H->b->dev;
     const int rl = rl_in_smem(b);
-    const int hvf = H->shape[dtype == KRY_C64 ? 1 : 0][1];
-    const int g = dtype == KRY_C64 ? vector_grid<float2>(b, rl, hvf, gridH, gridB)
-                                   : vector_grid<double2>(b, rl, hvf, gridH, gridB);
-    const int ov = H->shape[dtype == KRY_C64 ? 1 : 0][0];
+    const int hvf = H->shape[dtype_slot(dtype)][1];
+    const int g = dtype == KRY_C64    ? vector_grid<float2>(b, rl, hvf, gridH, gridB)
+                  : dtype == KRY_C128E ? vector_grid<dd2>(b, rl, hvf, gridH, gridB)
+                                       : vector_grid<double2>(b, rl, hvf, gridH, gridB);
+    const int ov = H->shape[dtype_slot(dtype)][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return (g > 0 && ov > 0) ? ov : g;   // vector_grid also sets the kernels' smem limits
 }
@@ -233,6 +235,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     }
     mark();
     if (rc == KRY_OK) rc = launch_smallexp(ea, cs, after_cond ? 0 : 1);
+    if constexpr (!std::is_same<V, dd2>::value) {
     if (rc == KRY_OK && opt && opt->vec_out) {
         VecOutArgs<V> va{};
         va.W = a.W;
@@ -244,10 +247,13 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         va.D = a.b.D;
         rc = launch_vecout<V>(va, gridB, cs);
     }
+    }   // (the vector outputs of the adjoint are complex128 or complex64 only)
     mark();
     if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, gridB, cs);
-    if (rc == KRY_OK && opt && opt->ckpt)
-        rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, gridB, cs);
+    if constexpr (!std::is_same<V, dd2>::value) {
+        if (rc == KRY_OK && opt && opt->ckpt)
+            rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, gridB, cs);
+    }
     mark();
     cudaError_t e = cudaStreamEndCapture(cs, &g);
     if (rc != KRY_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -283,7 +289,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     a.part = (double2 *)(base + l.oPart);
     a.ctl = (KryCtl *)(base + l.oCtl);
     a.rl_smem = rl_in_smem(b);
-    const int *shp = H->shape[dtype == KRY_C64 ? 1 : 0];
+    const int *shp = H->shape[dtype_slot(dtype)];
     a.hv_form = shp[1];
     a.dots_form = shp[2];
     a.upd_rows = shp[3];
@@ -477,7 +483,7 @@ int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
     const int Kp = padded_k(H->K);
     const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b), gridB)
                                    : batched_grid<double2>(b, Kp, rl_in_smem(b), gridB);
-    const int ov = H->shape[dtype == KRY_C64 ? 1 : 0][0];
+    const int ov = H->shape[dtype_slot(dtype)][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return g;
 }
@@ -561,7 +567,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     a.K = K;
     a.Kp = Kp;
     a.rl_smem = rl_in_smem(b);
-    a.kch = H->shape[dtype == KRY_C64 ? 1 : 0][4];
+    a.kch = H->shape[dtype_slot(dtype)][4];
     ExpArgsB ea{};
     ea.ctl = a.ctl;
     ea.times = (const double *)(base + l.oTimes);
@@ -707,9 +713,12 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
 int check_evolve_args(kry_ham H, int dtype, const double *times, int n_times, int m, double tol,
                       double *P_out)
 {
-    if (!H || !times || n_times < 1 || !P_out || m < 1 || m > MMAX || !(tol > 0.0) ||
-        (dtype != KRY_C128 && dtype != KRY_C64)) {
+    if (!H || !times || n_times < 1 || !P_out || m < 1 || m > MMAX || !(tol > 0.0) || !dtype_ok(dtype)) {
         set_error("kry_evolve: bad arguments (need H, times, n_times >= 1, P_out, 1 <= m <= %d, tol > 0)", MMAX);
+        return KRY_EINVAL;
+    }
+    if (dtype == KRY_C128E && (H->K > 1 || H->b->dev.list)) {
+        set_error("kry_evolve: KRY_C128E serves single-realisation evolutions on split-table bases (L <= 32)");
         return KRY_EINVAL;
     }
     for (int i = 0; i < n_times; ++i) {
@@ -755,7 +764,8 @@ extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *l
 
 extern "C" int64_t kry_workspace_bytes(kry_ham H, int dtype, int m, int n_times)
 {
-    if (!H || m < 1 || m > MMAX || n_times < 1 || (dtype != KRY_C128 && dtype != KRY_C64)) return -1;
+    if (!H || m < 1 || m > MMAX || n_times < 1 || !dtype_ok(dtype)) return -1;
+    if (dtype == KRY_C128E && (H->K > 1 || H->b->dev.list)) return -1;
     if (H->K > 1) {
         int gridB = 0;
         const int grid = grid_for_b(H, dtype, &gridB);
@@ -806,6 +816,8 @@ extern "C" int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double
     if (int rc = check_evolve_args(H, dtype, times, n_times, m, tol, P_out)) return rc;
     if (!d_psi0) { set_error("kry_evolve: d_psi0 is NULL"); return KRY_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == KRY_C128E)
+        return evolve_t<dd2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
@@ -826,6 +838,8 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
         return KRY_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == KRY_C128E)
+        return evolve_t<dd2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
@@ -863,6 +877,9 @@ int evolve_states(kry_ham H, int dtype, const uint64_t *states, const double *ti
                                         states, C_out);
     EvOpts opt;
     opt.C_out = C_out;
+    if (dtype == KRY_C128E)
+        return evolve_t<dd2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                             &opt);
     return dtype == KRY_C64
                ? evolve_t<float2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats,
                                   s, &opt)

@@ -214,10 +214,13 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr) return;
-    constexpr int KC = sizeof(V) == sizeof(float2) ? 32 : 64;   // columns (rows in flight per vector)
-    constexpr int NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, RT = 8, TR = KC * RT;
-    constexpr bool PF = PFT && sizeof(V) == sizeof(float2);   // prefetch (complex128 is FP64-bound: no gain)
-    using Acc = typename std::conditional<sizeof(V) == sizeof(float2), DotAccF2, DotAccD>::type;
+    constexpr bool DD = std::is_same<V, dd2>::value;   // FP64 storage, float-float arithmetic
+    constexpr bool F32 = std::is_same<V, float2>::value;
+    constexpr int KC = (F32 || DD) ? 32 : 64;          // columns (rows in flight per vector)
+    constexpr int RT = DD ? 4 : 8;                      // rows per column and tile
+    constexpr int NG = NTHR / KC, QD = (MMAX + NG - 1) / NG, TR = KC * RT;
+    constexpr bool PF = PFT && (F32 || DD);   // prefetch (complex128 is FP64-bound: no gain)
+    using Acc = typename std::conditional<F32, DotAccF2, DotAcc<V>>::type;
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wred[NTHR / 32][QD + 1];
     __shared__ int flag;
@@ -252,10 +255,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
         auto load = [&](const V *p, V *dst) {
             if (full) {
 #pragma unroll
-                for (int e = 0; e < RT; ++e) dst[e] = __ldg(p + r0 + KC * e);
+                for (int e = 0; e < RT; ++e) dst[e] = ldg(p + r0 + KC * e);
             } else {
 #pragma unroll
-                for (int e = 0; e < RT; ++e) dst[e] = (r0 + KC * e < D) ? __ldg(p + r0 + KC * e) : VT<V>::zero();
+                for (int e = 0; e < RT; ++e) dst[e] = (r0 + KC * e < D) ? ldg(p + r0 + KC * e) : VT<V>::zero();
             }
         };
         auto vec = [&](int q) { return a.W + (size_t)(q < A ? g + NG * q : xv) * a.ldW; };
@@ -265,6 +268,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
 #pragma unroll
             for (int e = 0; e < RT; ++e) nrm.add_norm(uu[e]);
         }
+        typename Arith<V>::Pre up[RT];   // y's rows prepared once for every vector of the tile
+#pragma unroll
+        for (int e = 0; e < RT; ++e) up[e] = pre(uu[e]);
         if (PF) {
             V nxt[RT];
             load(vec(0), cur);
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
                 if (q < nq) {
                     if (q + 1 < nq) load(vec(q + 1), nxt);
 #pragma unroll
-                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
+                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], up[e]);
 #pragma unroll
                     for (int e = 0; e < RT; ++e) cur[e] = nxt[e];
                 }
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
                 if (q < nq) {
                     load(vec(q), cur);
 #pragma unroll
-                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], uu[e]);
+                    for (int e = 0; e < RT; ++e) acc[q].add(cur[e], up[e]);
                 }
             }
         }
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
     if (MODE <= 1 && jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr2) return;
     const int nvec = (MODE == 2) ? ctl->m_eff : ((MODE == 3) ? 0 : jj + 1);
-    __shared__ V coef[MMAX + 1];
+    __shared__ typename Arith<V>::Coef coef[MMAX + 1];
     __shared__ double2 red[PSTRIDE];
     __shared__ double2 wtmp[NTHR / 32];
     __shared__ int flag;
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
     if (tid < PSTRIDE) red[tid] = make_double2(0.0, 0.0);
     if (tid < nvec) {
         const double2 c = (MODE == 0) ? ctl->coefA[tid] : (MODE == 1) ? ctl->coefC[tid] : ctl->coefY[tid];
-        coef[tid] = VT<V>::from(c);
+        coef[tid] = coef_from<V>(c);
     }
     __syncthreads();
     V *out = (MODE >= 2) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
@@ -413,9 +419,9 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
             in[k] = r + k * TILE < D;
             q[k] = in[k] ? r + k * TILE : r;   // past D a row repeats the first, unstored
         }
-        V w[RR];
+        typename Arith<V>::Lin w[RR];
 #pragma unroll
-        for (int k = 0; k < RR; ++k) w[k] = src ? src[q[k]] : VT<V>::zero();
+        for (int k = 0; k < RR; ++k) w[k] = lin_init(src ? src[q[k]] : VT<V>::zero());
         if (MODE == 2) {   // reads W_0 while overwriting it: plain loads
 #pragma unroll 8
             for (int i = 0; i < nvec; ++i) {
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
 #pragma unroll
                 for (int k = 0; k < RR; ++k) x[k] = wi[q[k]];
 #pragma unroll
-                for (int k = 0; k < RR; ++k) w[k] = cfms(coef[i], x[k], w[k]);
+                for (int k = 0; k < RR; ++k) lin_fms(w[k], coef[i], x[k]);
             }
         } else {
 #pragma unroll 8
@@ -432,17 +438,18 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
                 const V *wi = a.W + (size_t)i * a.ldW;
                 V x[RR];
 #pragma unroll
-                for (int k = 0; k < RR; ++k) x[k] = __ldg(wi + q[k]);
+                for (int k = 0; k < RR; ++k) x[k] = ldg(wi + q[k]);
 #pragma unroll
-                for (int k = 0; k < RR; ++k) w[k] = cfms(coef[i], x[k], w[k]);
+                for (int k = 0; k < RR; ++k) lin_fms(w[k], coef[i], x[k]);
             }
         }
 #pragma unroll
         for (int k = 0; k < RR; ++k) {
             if (!in[k]) continue;
-            out[q[k]] = w[k];
-            nrm.add_norm(w[k]);
-            if (a.G && MODE != 3) gacc.add(__ldg(a.G + q[k]), w[k]);
+            const V wv = (MODE == 3) ? src[q[k]] : lin_out(w[k]);   // (the load is a plain copy)
+            out[q[k]] = wv;
+            nrm.add_norm(wv);
+            if (a.G && MODE != 3) gacc.add(ldg(a.G + q[k]), wv);
         }
     }
     cta_sum_into(nrm, red, SLOT_NRM, wtmp);
@@ -708,8 +715,10 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
         return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
     };
     *gridH = fit(occH);
-    if (b.list) {
-        if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
+    if constexpr (!std::is_same<V, dd2>::value) {
+        if (b.list) {
+            if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
+        }
     }
     *gridB = fit(occB);
     return fit(occA);
@@ -718,7 +727,9 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
 template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
-    if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
+    if constexpr (!std::is_same<V, dd2>::value) {
+        if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
+    }
     EvArgs<V> ah = a;
     ah.rl_smem = a.rl_smem && !(a.hv_form & 2);
     const size_t smem = apply_smem(a.b, ah.rl_smem, sizeof(V) == sizeof(float2));
@@ -804,11 +815,15 @@ int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, 
 
 template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
 template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
+template int launch_dots<dd2>(const EvArgs<dd2> &, int, int, int, cudaStream_t, int);
 template int vector_grid<double2>(const DevBasis &, int, int, int *, int *);
 template int vector_grid<float2>(const DevBasis &, int, int, int *, int *);
+template int vector_grid<dd2>(const DevBasis &, int, int, int *, int *);
 template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);
 template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t, int);
+template int launch_hv<dd2>(const EvArgs<dd2> &, int, int, cudaStream_t, int);
 template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
 template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
+template int launch_lincomb<dd2>(const EvArgs<dd2> &, int, int, int, cudaStream_t, int);
 
 }  // namespace kry

@@ -12,6 +12,16 @@
 
 namespace kry {
 
+// A complex number stored in FP64 (the layout of double2) on which the vector kernels do
+// double-float arithmetic on the FP32 pipe (dtype KRY_C128E; see kry_device.cuh).
+struct __align__(16) dd2 {
+    double x, y;
+};
+
+// Index of a dtype's launch shape: KRY_C128, KRY_C64, KRY_C128E.
+inline int dtype_slot(int dtype) { return dtype == KRY_C64 ? 1 : (dtype == KRY_C128E ? 2 : 0); }
+inline bool dtype_ok(int dtype) { return dtype == KRY_C128 || dtype == KRY_C64 || dtype == KRY_C128E; }
+
 constexpr int MMAX = 32;       // largest Krylov dimension m (one warp holds the small problem)
 constexpr int TILE = 256;      // consecutive ranks per CTA tile
 constexpr int NTHR = 256;      // threads per CTA of the vector kernels
@@ -320,7 +330,7 @@ struct kry_ham_s {
     // eight gathers; bit 1: rank table through L1), [2] dots form (0 prefetch, 1 none), [3]
     // update rows per thread,
     // [4] batched H.v in chunks of this many realisations (0 = all K)
-    int shape[2][5];
+    int shape[3][5];
     int orth_check;             // measure <v_i, w> after every Lanczos update
     cudaStream_t cap_stream;
     cudaStream_t cap_stream2;   // captures the bodies of the step graph's conditional nodes
@@ -340,6 +350,6 @@ struct kry_ham_s {
 inline void default_shape(kry_ham_s *H, int Llo)
 {
     const int v[5] = {0, Llo >= 14 ? 3 : 0, 0, 2, 0};
-    for (int d = 0; d < 2; ++d)
+    for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 5; ++q) H->shape[d][q] = v[q];
 }

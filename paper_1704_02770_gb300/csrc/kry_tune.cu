@@ -44,32 +44,32 @@ bool valid_shape(const int *s)
 
 extern "C" int kry_set_grid(kry_ham H, int dtype, int grid)
 {
-    if (!H || grid < 0 || (dtype != KRY_C128 && dtype != KRY_C64)) {
+    if (!H || grid < 0 || !dtype_ok(dtype)) {
         set_error("kry_set_grid: bad arguments");
         return KRY_EINVAL;
     }
-    H->shape[dtype == KRY_C64 ? 1 : 0][0] = grid;
+    H->shape[dtype_slot(dtype)][0] = grid;
     return KRY_OK;
 }
 
 extern "C" int kry_set_shape(kry_ham H, int dtype, const int *shape)
 {
-    if (!H || !shape || (dtype != KRY_C128 && dtype != KRY_C64) || !valid_shape(shape)) {
+    if (!H || !shape || !dtype_ok(dtype) || !valid_shape(shape)) {
         set_error("kry_set_shape: bad arguments (shape = {grid >= 0, hv form 0..3, dots form 0|1, "
                   "update rows 1|2|4, batched chunk 0|8|16})");
         return KRY_EINVAL;
     }
-    for (int q = 0; q < NS; ++q) H->shape[dtype == KRY_C64 ? 1 : 0][q] = shape[q];
+    for (int q = 0; q < NS; ++q) H->shape[dtype_slot(dtype)][q] = shape[q];
     return KRY_OK;
 }
 
 extern "C" int kry_get_shape(kry_ham H, int dtype, int *shape)
 {
-    if (!H || !shape || (dtype != KRY_C128 && dtype != KRY_C64)) {
+    if (!H || !shape || !dtype_ok(dtype)) {
         set_error("kry_get_shape: bad arguments");
         return KRY_EINVAL;
     }
-    for (int q = 0; q < NS; ++q) shape[q] = H->shape[dtype == KRY_C64 ? 1 : 0][q];
+    for (int q = 0; q < NS; ++q) shape[q] = H->shape[dtype_slot(dtype)][q];
     return KRY_OK;
 }
 
@@ -78,14 +78,14 @@ extern "C" int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, d
                             void *stream)
 {
     if (!H || !shape_out || !n_cand || m < 1 || m > MMAX || !(t_probe > 0.0) || reps < 1 || max_cand < 0 ||
-        (max_cand > 0 && (!cand_out || !ms_out)) || (dtype != KRY_C128 && dtype != KRY_C64)) {
+        (max_cand > 0 && (!cand_out || !ms_out)) || !dtype_ok(dtype)) {
         set_error("kry_autotune: bad arguments");
         return KRY_EINVAL;
     }
     int dev = 0, sms = 0;
     KRY_CU(cudaGetDevice(&dev));
     KRY_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int slot = dtype == KRY_C64 ? 1 : 0;
+    const int slot = dtype_slot(dtype);
     int saved[NS], best[NS];
     for (int q = 0; q < NS; ++q) saved[q] = best[q] = H->shape[slot][q];
     std::vector<double> P((size_t)H->K);

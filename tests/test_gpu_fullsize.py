@@ -16,8 +16,8 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-BAR = {"c128": 1e-10, "c64": 1e-5}
-TOL = {"c128": 1e-10, "c64": 1e-7}
+BAR = {"c128": 1e-10, "c64": 1e-5, "c128e": 1e-10}
+TOL = {"c128": 1e-10, "c64": 1e-7, "c128e": 1e-10}
 
 
 def _report(name, err):
@@ -38,7 +38,7 @@ def _golden_P(name, cols="t P"):
     return {k: (np.array(v[0]), np.array(v[1])) for k, v in out.items()}
 
 
-@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "c128e"])
 def test_L24_all_output_times_vs_oracle(kry, dtype):
     """The L = 24 workload (D = 2,704,156) at all 40 output times, t = 0.1 .. 100: 143 and
     more Krylov steps, so step boundaries, dense output and the step-size control are all
@@ -104,13 +104,13 @@ def test_L20_gradient_vs_oracle_differences(kry):
 @pytest.mark.parametrize("name", ["L30_clean", "L30_qp"])
 def test_L30_early_times_vs_moment_series(kry, name):
     """The L = 30 workloads (D = 155,117,520) at the output times the oracle's moment series
-    reaches with a rigorous error bound <= 1e-12, in complex128 (84 GB of Krylov workspace)
-    and complex64."""
+    reaches with a rigorous error bound <= 1e-12, in complex128 (84 GB of Krylov workspace),
+    complex64, and complex128 with float-float arithmetic."""
     c = workloads.config(name)
     times, Po = _golden_P(f"P_{name}_early.txt", "t P bound")[0]
     assert len(times) >= 3 and np.allclose(times, c["times"][:len(times)], rtol=0, atol=0)
     B = kry.Basis(c["L"], c["n_up"])
-    for dtype in ("c128", "c64"):
+    for dtype in ("c128", "c64", "c128e"):
         H = kry.Hamiltonian(B, c["J"], c["Delta"], c["h"][0], pbc=c["pbc"])
         P, st = H.return_probability(c["state"], list(times), m=c["m"], tol=TOL[dtype], dtype=dtype)
         H.close()
