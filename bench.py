@@ -397,6 +397,17 @@ def run_ours(args):
                                 "max_abs_dP_vs_fp64_tol_1e-10": float(np.max(np.abs(P7 - P128)))}
         out["mixed"]["time_to_solution_speedup_vs_fp64_same_tol"] = s7 / s64
         out["mixed"]["krylov_steps_per_step"] = st64["n_krylov_steps"]
+        # complex128 vectors with float-float arithmetic on the FP32 pipe, at the FP64 tol
+        sece, hve, le, Pe, ste, profe = timed("c128e", c["tol"], profile=True)
+        ue, se_ = aggregate(D * hve, sece, world)
+        out["gpu_launches"] += le
+        out["fp64_emulated"] = {
+            "dtype": "c128 storage, float-float arithmetic on the FP32 pipe (about 47 bits)",
+            "value": ue / se_, "unit": "state-updates/s", "ms_per_step": 1e3 * se_ / args.steps,
+            "tol": c["tol"], "speedup_vs_fp64": (ue / se_) / value,
+            "krylov_steps_per_step": ste["n_krylov_steps"],
+            "max_abs_dP_vs_fp64": float(np.max(np.abs(Pe - P128))),
+            "roofline": roofline(profe, "c128e", D, c, L, N, clocks, traffic_key="e_")}
     # batched realisations: the K = 64 phase ensemble of L = 22 in one interleaved launch
     if not args.no_batched:
         cb = workloads.config("L22_batched_h1.5")
