@@ -28,7 +28,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Krylov H.v state-updates/s (+ % HBM roofline), FP64 vs FP32/batched at set error"
 WORKLOAD = "L24_mixed"
 HBM_PEAK_FALLBACK = 6800.0
-KIND_NAMES = ("passA", "passB", "passC", "smallexp", "combine")
+# profiled kernel kinds: pass A's H.v (k_hv) and dots (k_dots<.,0>), pass B's update
+# (k_lincomb<.,0>), pass C (the second Gram-Schmidt pass), the small exponential, the combine
+KIND_NAMES = ("hv", "dots", "update", "passC", "smallexp", "combine")
+KERNEL_OF = {"hv": "k_hv", "dots": "k_dots<.,0>", "update": "k_lincomb<.,0>",
+             "passC": "k_dots<.,1> + k_lincomb<.,1>", "smallexp": "k_smallexp", "combine": "k_lincomb<.,2>"}
+# vector passes (reads + writes of D-element vectors) per launch at Lanczos index j
+PASSES = {"hv": lambda j: 2, "dots": lambda j: j + 2, "update": lambda j: j + 3}
 
 
 def parse():
@@ -160,7 +166,7 @@ def ncu_traffic(kind, algo_bytes_per_launch):
     """DRAM bytes per (average) launch of `kind`: the committed ncu capture of one launch,
     scaled by algorithmic bytes to the average launch; None if the kernel sources no
     longer hash to the value recorded with the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic_L24.txt")
+    path = os.path.join(ROOT, "profiles", "traffic_vector_kernels.txt")
     try:
         rows = dict(line.strip().split("=", 1) for line in open(path)
                     if "=" in line and not line.startswith("#"))
@@ -177,15 +183,15 @@ def ncu_traffic(kind, algo_bytes_per_launch):
 def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
     """Algorithmic FP64 flops of all launches of `kind` over `krylov_steps` full steps.
 
-    Per element: a complex multiply-add is 8 flops, |w|^2 is 4.  Pass A at Lanczos index j
-    does the H.v row (2 flops per gathered neighbour, 10 for the diagonal term and the
-    J/2 scale), j+1 dots and ||u||^2; pass B does j+1 updates and ||w||^2 (its second
-    Gram-Schmidt pass runs only when flagged and is counted under pass C).
+    Per element: a complex multiply-add is 8 flops, |w|^2 is 4.  At Lanczos index j the H.v
+    row costs 2 flops per gathered neighbour and 10 for the diagonal term and the J/2 scale;
+    the dots j+1 complex multiply-adds and ||u||^2; the update j+1 complex multiply-adds and
+    ||w||^2 (the second Gram-Schmidt pass runs only when flagged and is counted under pass C).
     The average number of neighbours is 2N(L-N)/(L-1) on a ring, 2N(L-N)/L open."""
     nb = 2.0 * N * (L - N) / ((L - 1) if pbc else L)
-    if kind == "passA":
-        per = sum(8 * (j + 1) + 4 + 10 + 2 * nb for j in range(m))
-    elif kind == "passB":
+    if kind == "hv":
+        per = m * (10 + 2 * nb)
+    elif kind in ("dots", "update"):
         per = sum(8 * (j + 1) + 4 for j in range(m))
     else:
         return 0.0
@@ -195,13 +201,13 @@ def fp64_flops(kind, D, m, krylov_steps, L, N, pbc):
 def fp64_pipe_ops(kind, D, m, krylov_steps, L, N, pbc):
     """FP64 pipe instructions (per thread-element) of all launches of `kind`: a fused
     multiply-add, a multiply and an add each occupy the pipe once, so the adds of the H.v
-    (two per gathered neighbour) cost as much pipe time as multiply-adds.  Pass A at index j:
-    2 per neighbour and 7 for the diagonal term and the scales, 4 per dot (j+1 of them) and 2
-    for ||u||^2; pass B: 4 per update (j+1) and 2 for ||w||^2."""
+    (two per gathered neighbour) cost as much pipe time as multiply-adds.  At index j: the
+    H.v 2 per neighbour and 7 for the diagonal term and the scales; the dots 4 per vector
+    (j+1) and 2 for ||u||^2; the update 4 per vector (j+1) and 2 for ||w||^2."""
     nb = 2.0 * N * (L - N) / ((L - 1) if pbc else L)
-    if kind == "passA":
-        per = sum(4 * (j + 1) + 2 + 7 + 2 * nb for j in range(m))
-    elif kind == "passB":
+    if kind == "hv":
+        per = m * (7 + 2 * nb)
+    elif kind in ("dots", "update"):
         per = sum(4 * (j + 1) + 2 for j in range(m))
     else:
         return 0.0
@@ -220,7 +226,7 @@ def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
     HBM."""
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks and "hbm_gbs" in peaks else HBM_PEAK_FALLBACK
-    dom = max(KIND_NAMES, key=lambda k: prof[k]["ms"])
+    dom = max(("hv", "dots", "update"), key=lambda k: prof[k]["ms"])   # the dominant kernel
     per = {k: {"ms": round(prof[k]["ms"], 3),
                "GBps": (prof[k]["bytes"] / (prof[k]["ms"] * 1e6)) if prof[k]["ms"] else None,
                "launches": prof[k]["launches"]} for k in KIND_NAMES}
@@ -234,8 +240,8 @@ def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
     share = {k: prof[k]["ms"] / sum(prof[q]["ms"] for q in KIND_NAMES) for k in KIND_NAMES}
     if form == "c128":
         # Krylov steps that did work (replays after the last output time are no-ops):
-        # recovered from the kind's algorithmic bytes, (j+4) or (j+3) vectors at index j
-        per_step = sum((j + 4) if dom == "passA" else (j + 3) for j in range(c["m"])) * D * 16
+        # recovered from the kernel's algorithmic bytes, PASSES[dom](j) vectors at index j
+        per_step = sum(PASSES[dom](j) for j in range(c["m"])) * D * 16
         steps = prof[dom]["bytes"] / per_step
         fl = fp64_flops(dom, D, c["m"], steps, L, N, c["pbc"])
         mhz = clocks["sm_mhz"] or 2070.0
@@ -254,14 +260,14 @@ def roofline(prof, form, D, c, L, N, clocks, traffic_key=None):
         pipe = {"achieved": ach_ops, "peak": ops_peak, "unit": "T FP64 instr/s", "frac": ach_ops / ops_peak,
                 "peak_source": "the measured multiply-add rate, one instruction each",
                 "note": "adds occupy the pipe like multiply-adds; the H.v is add-heavy"}
-        return {"bound": "alu", "kernel": dom, "achieved": ach_fl, "peak": fp64_peak,
+        return {"bound": "alu", "kernel": KERNEL_OF[dom], "kind": dom, "achieved": ach_fl, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": ach_fl / fp64_peak,
                 "peak_source": src,
                 "traffic": tr, "algo_bytes_per_launch": prof[dom]["bytes"] / nl,
                 "fp64_pipe_view": pipe,
                 "hbm_view": hbm, "per_kind": per, "kernel_time_share": share,
                 "profiled_region_s": prof.get("_sec"), "timing": TIMING_NOTE}
-    return dict(bound="hbm", kernel=dom, traffic=tr, algo_bytes_per_launch=prof[dom]["bytes"] / nl,
+    return dict(bound="hbm", kernel=KERNEL_OF[dom], kind=dom, traffic=tr, algo_bytes_per_launch=prof[dom]["bytes"] / nl,
                 per_kind=per, kernel_time_share=share, profiled_region_s=prof.get("_sec"),
                 timing=TIMING_NOTE, **hbm)
 
@@ -509,8 +515,8 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
     """The largest single-GPU configuration: L = 30, N_up = 15 (D = 155,117,520), Neel state,
     m = 30, 40 log times to t = 100.  Default: the quasiperiodic field (h = 1.5) in complex64
     (42 GB of Krylov workspace), one evolution after a short capture run.  full: both fields,
-    complex128 (84 GB) and complex64, and the end-to-end call with psi0 copied from pinned host
-    memory.  One evolution per case, with CUDA event nodes between the kernels for the
+    complex128 (84 GB), complex64 and complex128 with float-float vectors (84 GB), and the
+    end-to-end call with psi0 copied from pinned host memory.  One evolution per case, with CUDA event nodes between the kernels for the
     per-kind times (at this size their overhead is far below a kernel's duration)."""
     import numpy as np
     import torch
@@ -519,7 +525,8 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
            "timing": "one evolution per case after a capture run to t=0.1; per-kind times from event "
                      "nodes in the same run"}
     launches = 0
-    cases = [("L30_qp", "c64")] if not full else [(n, d) for n in ("L30_clean", "L30_qp") for d in ("c64", "c128")]
+    cases = ([("L30_qp", "c64")] if not full else
+             [(n, d) for n in ("L30_clean", "L30_qp") for d in ("c64", "c128", "c128e")])
     B = None
     for name, dt in cases:
         c = workloads.config(name)
@@ -530,7 +537,7 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
         # launch shape tuned on this sector (one Krylov step per probe)
         t_ = H.autotune(c["state"], 0.02, dtype=dt, reps=1)
         res.setdefault("autotune", {})[f"{name}_{dt}"] = t_
-        tol = c["tol"] if dt == "c128" else 1e-7
+        tol = 1e-7 if dt == "c64" else c["tol"]
         H.return_probability(c["state"], [0.1], m=c["m"], tol=tol, dtype=dt)
         H.profile(True)
         H.return_probability(c["state"], [0.1], m=c["m"], tol=tol, dtype=dt)   # instrumented capture
@@ -576,9 +583,12 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
         torch.cuda.empty_cache()
     if full:
         for name in ("L30_clean", "L30_qp"):
-            a, b = res.get(f"{name}_c128"), res.get(f"{name}_c64")
-            if a and b:
-                b["speedup_vs_fp64"] = b["value"] / a["value"]
+            a = res.get(f"{name}_c128")
+            for dt in ("c64", "c128e"):
+                b = res.get(f"{name}_{dt}")
+                if a and b:
+                    b["speedup_vs_fp64"] = b["value"] / a["value"]
+                    b["time_to_solution_speedup_vs_fp64"] = a["ms_per_step"] / b["ms_per_step"]
     res["_launches"] = launches
     return res
 

@@ -53,11 +53,12 @@ enum {
 enum { KRY_OBC = 0, KRY_PBC = 1 };
 /* Element types of the state vectors.  KRY_C128: complex128 with FP64 arithmetic.  KRY_C64:
  * complex64 vectors and H.v, FP64 Lanczos coefficients and FP64-grade (float-float) dots.
- * KRY_C128E: complex128 storage (the same vectors as KRY_C128) with the vector arithmetic
- * (H.v sums, dots, updates) done in float-float on the FP32 pipe, about 47 significant bits,
- * because GB300 runs FP64 at 1/64 of its FP32 rate; the Lanczos coefficients, the small
- * exponential and the step control stay FP64.  KRY_C128E serves single-realisation
- * evolutions (K = 1) on split-table bases (L <= 32); elsewhere it returns KRY_EINVAL. */
+ * KRY_C128E: complex128 in and out (the same arguments as KRY_C128), with the Krylov vectors
+ * held as float-float pairs (16 bytes per element, about 48 significant bits) and the vector
+ * arithmetic (H.v sums, dots, updates) done in float-float on the FP32 pipe, because GB300
+ * runs FP64 at 1/64 of its FP32 rate; the Lanczos coefficients, the small exponential and the
+ * step control stay FP64.  KRY_C128E serves single-realisation evolutions (K = 1) on
+ * split-table bases (L <= 32); elsewhere it returns KRY_EINVAL. */
 enum { KRY_C128 = 0, KRY_C64 = 1, KRY_C128E = 2 };
 
 /* Counters of one kry_evolve / kry_return_probability call. */
@@ -214,13 +215,15 @@ int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, dou
  * kernels in every Lanczos index (returning at once unless needed) instead of through a
  * conditional node: external profilers such as Nsight Compute cannot see the kernels of a
  * graph that has conditional nodes.  KRY_EINVAL for other values.
- * kry_profile_read fills, for the five kernel kinds
- *   0 = pass A (H.v fused with the reorthogonalisation dots), 1 = pass B (Lanczos update
- *   with the second-pass dots), 2 = pass C (second-pass correction), 3 = small
- *   exponential and step control, 4 = combine psi = beta V y,
+ * kry_profile_read fills, for the six kernel kinds
+ *   0 = pass A's dots (<v_i, u> for i <= j, alpha_j and ||u||^2), 1 = pass B (the Lanczos
+ *   update w = u - sum c_i v_i and ||w||^2), 2 = pass C (the second Gram-Schmidt pass, when
+ *   flagged), 3 = small exponential and step control, 4 = combine psi = beta V y,
+ *   5 = pass A's H.v (u = sigma_j (H - s) v_j),
  * the summed event time in ms, the algorithmic HBM bytes (vector reads and writes by
- * formula; gathers of H.v beyond one read of v_j are not counted) and the launch count,
- * accumulated since the last kry_profile_enable(H, 1).  Arrays have 5 entries, host. */
+ * formula; gathers of H.v beyond one read of v_j are not counted) and the count of
+ * profiled intervals, accumulated since the last kry_profile_enable(H, 1).  Arrays have 6
+ * entries, host. */
 int kry_profile_enable(kry_ham H, int on);
 int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
 

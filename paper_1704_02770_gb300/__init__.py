@@ -15,8 +15,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libkry_gb300.so")
 KRY_OK, KRY_EINVAL, KRY_ENOMEM, KRY_ETOL, KRY_ETIMEOUT, KRY_ECUDA = range(6)
 KRY_OBC, KRY_PBC = 0, 1
 KRY_C128, KRY_C64, KRY_C128E = 0, 1, 2
-# dtype names: complex128 (FP64 arithmetic), complex64 (mixed precision), and complex128
-# storage with float-float arithmetic on the FP32 pipe
+# dtype names: complex128 (FP64 arithmetic), complex64 (mixed precision), and complex128 in
+# and out with float-float vectors and arithmetic on the FP32 pipe inside
 _CODES = {"c128": KRY_C128, "complex128": KRY_C128, "c64": KRY_C64, "complex64": KRY_C64,
           "c128e": KRY_C128E}
 MMAX = 32
@@ -333,12 +333,13 @@ class Hamiltonian:
         (kry_profile_enable)."""
         _check(load().kry_profile_enable(self._h, int(on)))
 
-    KINDS = ("passA", "passB", "passC", "smallexp", "combine")
+    # pass A's dots, pass B's update, pass C, the small exponential, the combine, pass A's H.v
+    KINDS = ("dots", "update", "passC", "smallexp", "combine", "hv")
 
     def profile_read(self):
         import numpy as np
-        ms, by = np.zeros(5), np.zeros(5)
-        n = (ctypes.c_int64 * 5)()
+        ms, by = np.zeros(6), np.zeros(6)
+        n = (ctypes.c_int64 * 6)()
         _check(load().kry_profile_read(self._h, ms.ctypes.data_as(_dp), by.ctypes.data_as(_dp), n))
         return {k: dict(ms=float(ms[i]), bytes=float(by[i]), launches=int(n[i]))
                 for i, k in enumerate(self.KINDS)}

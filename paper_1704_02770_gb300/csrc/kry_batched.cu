@@ -451,8 +451,9 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
     if (mode == 0) {
         if (k == 0) {
             H.n_hv += 1;
-            H.vec_passes += (double)(jj + 2);
-            H.vp_kind[0] += (double)(jj + 2);
+            H.vec_passes += (double)(jj + 4);
+            H.vp_kind[KIND_PASSA] += (double)(jj + 2);   // u and v_0 .. v_j
+            H.vp_kind[KIND_HV] += 2.0;                  // the H.v: v_j read, u written
             H.corr_any = 0;
             H.dots_any = 0;
         }
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
     } else if (mode == 1) {
         if (k == 0) {
             H.vec_passes += (double)(jj + 3) + (general ? 1.0 : 0.0);
-            H.vp_kind[1] += (double)(jj + 3) + (general ? 1.0 : 0.0);
+            H.vp_kind[KIND_PASSB] += (double)(jj + 3) + (general ? 1.0 : 0.0);
         }
         ctl->corr[k] = 0;
         ctl->dots[k] = 0;
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
     } else if (mode == 3) {
         if (k == 0) {
             H.vec_passes += (double)(jj + 2);
-            H.vp_kind[2] += (double)(jj + 2);
+            H.vp_kind[KIND_PASSC] += (double)(jj + 2);
         }
         if (!ctl->dots[k] || jj >= ctl->m_eff[k]) return;
         double nd2 = 0.0;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(128) k_reduce_b(KryCtlB *ctl, const double2 *_
     } else if (mode == 2) {
         if (k == 0) {
             H.vec_passes += (double)(jj + 3) + (general ? 1.0 : 0.0);
-            H.vp_kind[2] += (double)(jj + 3) + (general ? 1.0 : 0.0);
+            H.vp_kind[KIND_PASSC] += (double)(jj + 3) + (general ? 1.0 : 0.0);
         }
         if (jj < ctl->m_eff[k] && ctl->corr[k]) {
             atomicAdd(&H.n_corr, 1ull);
@@ -545,7 +546,7 @@ __global__ void k_step_done_b(KryCtlB *ctl, int general)
     H.err_sum += e;
     H.n_steps += 1;
     H.vec_passes += (double)(H.m_run + 1) + (general ? 1.0 : 0.0);
-    H.vp_kind[4] += (double)(H.m_run + 1) + (general ? 1.0 : 0.0);
+    H.vp_kind[KIND_COMBINE] += (double)(H.m_run + 1) + (general ? 1.0 : 0.0);
     H.t_now = H.t_next;
     H.next_out = H.next_out_new;
     H.m_run = H.m;
@@ -636,12 +637,18 @@ int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB)
 }
 
 // pass A: the H.v at full occupancy (its own grid), then the dots on the common grid
-// (their partials feed k_reduce_b)
+// (their partials feed k_reduce_b); part 1 launches the H.v alone, part 2 the dots alone
 template <class V>
-int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
+int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s, int part)
 {
+    if (part == 2) {
+        KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
+        KRY_CU(cudaGetLastError());
+        return KRY_OK;
+    }
     if (a.b.list) {
         if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
+        if (part == 1) return KRY_OK;
         KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
         KRY_CU(cudaGetLastError());
         return KRY_OK;
@@ -663,14 +670,12 @@ int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s)
             k_hv_bc<V, 16><<<hv_grid(k_hv_bc<V, 16>, items), NTHR, sH, s>>>(a, jj);
         }
         KRY_CU(cudaGetLastError());
-        KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
+    } else {
+        KRY_KQ_SWITCH(a.Kp, { k_hv_b<V, KQ><<<hv_grid(k_hv_b<V, KQ>, ntiles), NTHR, sH, s>>>(a, jj); });
         KRY_CU(cudaGetLastError());
-        return KRY_OK;
     }
-    KRY_KQ_SWITCH(a.Kp, {
-        k_hv_b<V, KQ><<<hv_grid(k_hv_b<V, KQ>, ntiles), NTHR, sH, s>>>(a, jj);
-        k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj);
-    });
+    if (part == 1) return KRY_OK;
+    KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -742,8 +747,8 @@ int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaS
 
 template int batched_grid<double2>(const DevBasis &, int, int, int *);
 template int batched_grid<float2>(const DevBasis &, int, int, int *);
-template int launch_passA_b<double2>(const EvArgsB<double2> &, int, int, cudaStream_t);
-template int launch_passA_b<float2>(const EvArgsB<float2> &, int, int, cudaStream_t);
+template int launch_passA_b<double2>(const EvArgsB<double2> &, int, int, cudaStream_t, int);
+template int launch_passA_b<float2>(const EvArgsB<float2> &, int, int, cudaStream_t, int);
 template int launch_lincomb_b<double2>(const EvArgsB<double2> &, int, int, int, cudaStream_t);
 template int launch_lincomb_b<float2>(const EvArgsB<float2> &, int, int, int, cudaStream_t);
 

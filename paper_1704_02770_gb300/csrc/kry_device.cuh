@@ -26,16 +26,19 @@ template <> struct VT<float2> {
     __device__ __forceinline__ static float2 from(double2 c) { return make_float2((float)c.x, (float)c.y); }
 };
 
-// ---------------------------------------------------------------- FP64 storage, FP32-pipe arithmetic
+// ---------------------------------------------------------------- float-float vectors
 // GB300 runs FP64 arithmetic, and conversions between FP64 and FP32, at 1/64 of its FP32
 // rate, so the complex128 passes are bound by the FP64 pipe at about a third of the HBM rate.
-// The element type dd2 (kry_internal.cuh) keeps the vectors in FP64 (the layout of double2)
-// and does the vector arithmetic on the FP32 pipe: every double is split by integer operations on its bits into
-// hi + lo floats (its leading 24 significant bits and the next 23, both truncated), products
-// are formed exactly for the hi parts (the fused multiply-add error term) with the cross
-// terms in float, and sums are float-float (Knuth's TwoSum).  The arithmetic carries about 47
-// significant bits (relative error of a dot product about 2^-47 of the sum of |terms|, where
-// FP64 gives 2^-53); each result is rounded back to FP64 with one FP64 add.
+// dtype KRY_C128E keeps the Krylov vectors as float-float pairs (ffc, kry_internal.cuh: 16
+// bytes per element like complex128, about 48 significant bits) and does all vector
+// arithmetic on the FP32 pipe: products are formed exactly for the leading parts (the fused
+// multiply-add error term) with the cross terms in float, and sums are float-float (Knuth's
+// TwoSum).  A dot product is accurate to about 2^-47 of the sum of |terms| (FP64: 2^-53).
+// Complex128 inputs and coefficients are converted at the boundary: a double is split by
+// integer operations on its bits into its leading 24 significant bits and the next 23.
+
+__device__ __forceinline__ void ff_combine(float &s, float &c, float s2, float c2);
+
 // hi + lo floats of x (|x| in [2^-80, 2^128); smaller magnitudes give 0, which for vectors of
 // norm of order one changes a dot product by less than 2^-80 D^(1/2))
 __device__ __forceinline__ float2 dsplit(double x)
@@ -49,8 +52,6 @@ __device__ __forceinline__ float2 dsplit(double x)
     const float sc = __uint_as_float(ok ? (sg | ((ex - 942u) << 23)) : 0u);                            // +-2^(e-46)
     return make_float2(hi, __fmul_rn(lm, sc));
 }
-__device__ __forceinline__ void ff_combine(float &s, float &c, float s2, float c2);
-
 // a float as a double, exactly, by integer operations (zero and subnormal floats give 0)
 __device__ __forceinline__ double f2d(float f)
 {
@@ -61,8 +62,8 @@ __device__ __forceinline__ double f2d(float f)
 }
 // float-float s + c rounded to FP64 (one FP64 add)
 __device__ __forceinline__ double ff2d(float s, float c) { return f2d(s) + f2d(c); }
-// (s, c) += (ah + al)(bh + bl): the hi product split exactly (TwoSum into s), the error term and
-// the cross terms into c
+// (s, c) += (ah + al)(bh + bl): the leading product split exactly (TwoSum into s), the error
+// term and the cross terms into c
 __device__ __forceinline__ void ff_mac(float ah, float al, float bh, float bl, float &s, float &c)
 {
     const float p = __fmul_rn(ah, bh);
@@ -75,19 +76,32 @@ __device__ __forceinline__ void ff_mac(float ah, float al, float bh, float bl, f
     s = t;
     c = __fadd_rn(c, __fadd_rn(err, e));
 }
+// (s, c) renormalised so that |c| is at most half an ulp of s (TwoSum: exact for any order of
+// magnitudes, so also after a cancellation has left |c| > |s|)
+__device__ __forceinline__ void ff_renorm(float &s, float &c)
+{
+    const float t = __fadd_rn(s, c);
+    const float z = __fsub_rn(t, s);
+    c = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(c, z));
+    s = t;
+}
 
-template <> struct VT<dd2> {
+template <> struct VT<ffc> {
     using R = double;
-    __device__ __forceinline__ static dd2 zero() { return dd2{0.0, 0.0}; }
+    __device__ __forceinline__ static ffc zero() { return ffc{0.f, 0.f, 0.f, 0.f}; }
     __device__ __forceinline__ static double ehlo(const DevHam &h, uint32_t p) { return __ldg(h.ehlo_d + p); }
     __device__ __forceinline__ static double ehhi(const DevHam &h, uint32_t p) { return __ldg(h.ehhi_d + p); }
     __device__ __forceinline__ static double eh8(const DevHam &h, size_t p) { return __ldg(h.eh8_d + p); }
-    __device__ __forceinline__ static dd2 from(double2 c) { return dd2{c.x, c.y}; }
+    __device__ __forceinline__ static ffc from(double2 c)
+    {
+        const float2 a = dsplit(c.x), b = dsplit(c.y);
+        return ffc{a.x, a.y, b.x, b.y};
+    }
 };
-__device__ __forceinline__ dd2 ldg(const dd2 *p)
+__device__ __forceinline__ ffc ldg(const ffc *p)
 {
-    const double2 v = __ldg((const double2 *)p);
-    return dd2{v.x, v.y};
+    const float4 v = __ldg((const float4 *)p);
+    return ffc{v.x, v.y, v.z, v.w};
 }
 __device__ __forceinline__ float2 ldg(const float2 *p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldg(const double2 *p) { return __ldg(p); }
@@ -104,11 +118,11 @@ template <class V> struct Arith {
     using Coef = V;
     using Pre = V;
 };
-template <> struct Arith<dd2> {
+template <> struct Arith<ffc> {
     using HvSum = FF4;
     using Lin = FF4;
     using Coef = float4;   // (re hi, re lo, im hi, im lo)
-    using Pre = float4;
+    using Pre = ffc;
 };
 
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -135,38 +149,43 @@ __device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a)
 }
 // neighbour sums of the H.v row: acc += v, then y = sd x + shj acc
 template <class V> __device__ __forceinline__ void hv_add(V &acc, V v) { acc = acc + v; }
-__device__ __forceinline__ void hv_add(FF4 &acc, dd2 v)
+__device__ __forceinline__ void hv_add(FF4 &acc, ffc v)
 {
-    const float2 a = dsplit(v.x), b = dsplit(v.y);
-    ff_combine(acc.sr, acc.cr, a.x, a.y);
-    ff_combine(acc.si, acc.ci, b.x, b.y);
+    ff_combine(acc.sr, acc.cr, v.xh, v.xl);
+    ff_combine(acc.si, acc.ci, v.yh, v.yl);
 }
 __device__ __forceinline__ double2 axpby(double d, double2 x, double s, double2 a);
 __device__ __forceinline__ float2 axpby(float d, float2 x, float s, float2 a);
 template <class V, class R> __device__ __forceinline__ V hv_finish(R sd, V x, R shj, V acc) { return axpby(sd, x, shj, acc); }
-__device__ __forceinline__ dd2 hv_finish(double sd, dd2 x, double shj, const FF4 &acc)
+__device__ __forceinline__ ffc hv_finish(double sd, ffc x, double shj, const FF4 &acc)
 {
-    const float2 d = dsplit(sd), h = dsplit(shj), xr = dsplit(x.x), xi = dsplit(x.y);
+    const float2 d = dsplit(sd), h = dsplit(shj);
     float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    ff_mac(d.x, d.y, xr.x, xr.y, sr, cr);
+    ff_mac(d.x, d.y, x.xh, x.xl, sr, cr);
     ff_mac(h.x, h.y, acc.sr, acc.cr, sr, cr);
-    ff_mac(d.x, d.y, xi.x, xi.y, si, ci);
+    ff_mac(d.x, d.y, x.yh, x.yl, si, ci);
     ff_mac(h.x, h.y, acc.si, acc.ci, si, ci);
-    return dd2{ff2d(sr, cr), ff2d(si, ci)};
+    ff_renorm(sr, cr);
+    ff_renorm(si, ci);
+    return ffc{sr, cr, si, ci};
 }
 // linear combinations: w = src - sum_i c_i x_i
 template <class V> __device__ __forceinline__ V lin_init(V src) { return src; }
 template <class V> __device__ __forceinline__ V lin_out(V w) { return w; }
 template <class V> __device__ __forceinline__ typename Arith<V>::Coef coef_from(double2 c) { return VT<V>::from(c); }
-__device__ __forceinline__ FF4 lin_init(dd2 src)
+__device__ __forceinline__ FF4 lin_init(ffc src)
 {
-    const float2 a = dsplit(src.x), b = dsplit(src.y);
     FF4 w;
-    w.sr = a.x; w.cr = a.y; w.si = b.x; w.ci = b.y;
+    w.sr = src.xh; w.cr = src.xl; w.si = src.yh; w.ci = src.yl;
     return w;
 }
-__device__ __forceinline__ dd2 lin_out(const FF4 &w) { return dd2{ff2d(w.sr, w.cr), ff2d(w.si, w.ci)}; }
-template <> __device__ __forceinline__ float4 coef_from<dd2>(double2 c)
+__device__ __forceinline__ ffc lin_out(FF4 w)
+{
+    ff_renorm(w.sr, w.cr);
+    ff_renorm(w.si, w.ci);
+    return ffc{w.sr, w.cr, w.si, w.ci};
+}
+template <> __device__ __forceinline__ float4 coef_from<ffc>(double2 c)
 {
     const float2 a = dsplit(c.x), b = dsplit(c.y);
     return make_float4(a.x, a.y, b.x, b.y);
@@ -174,22 +193,16 @@ template <> __device__ __forceinline__ float4 coef_from<dd2>(double2 c)
 __device__ __forceinline__ double2 cfms(double2 c, double2 v, double2 w);
 __device__ __forceinline__ float2 cfms(float2 c, float2 v, float2 w);
 template <class V> __device__ __forceinline__ void lin_fms(V &w, V c, V x) { w = cfms(c, x, w); }
-__device__ __forceinline__ void lin_fms(FF4 &w, float4 c, dd2 x)
+__device__ __forceinline__ void lin_fms(FF4 &w, float4 c, ffc x)
 {
     // w -= c x: re -= cr xr - ci xi, im -= cr xi + ci xr
-    const float2 xr = dsplit(x.x), xi = dsplit(x.y);
-    ff_mac(-c.x, -c.y, xr.x, xr.y, w.sr, w.cr);
-    ff_mac(c.z, c.w, xi.x, xi.y, w.sr, w.cr);
-    ff_mac(-c.x, -c.y, xi.x, xi.y, w.si, w.ci);
-    ff_mac(-c.z, -c.w, xr.x, xr.y, w.si, w.ci);
+    ff_mac(-c.x, -c.y, x.xh, x.xl, w.sr, w.cr);
+    ff_mac(c.z, c.w, x.yh, x.yl, w.sr, w.cr);
+    ff_mac(-c.x, -c.y, x.yh, x.yl, w.si, w.ci);
+    ff_mac(-c.z, -c.w, x.xh, x.xl, w.si, w.ci);
 }
 // a right-hand vector element prepared for several dot products
 template <class V> __device__ __forceinline__ V pre(V u) { return u; }
-__device__ __forceinline__ float4 pre(dd2 u)
-{
-    const float2 a = dsplit(u.x), b = dsplit(u.y);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 
 __device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
@@ -348,24 +361,20 @@ struct DotAccF2 {
     }
 };
 
-// sum conj(a) b for FP64-stored vectors in float-float arithmetic (dd2)
-struct DotAccDD {
+// sum conj(a) b for float-float vectors (ffc)
+struct DotAccFF {
     float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    // b prepared by pre(): (bx hi, bx lo, by hi, by lo)
-    __device__ __forceinline__ void add(dd2 a, float4 b)
+    __device__ __forceinline__ void add(ffc a, ffc b)
     {
-        const float2 ax = dsplit(a.x), ay = dsplit(a.y);
-        ff_mac(ax.x, ax.y, b.x, b.y, sr, cr);
-        ff_mac(ay.x, ay.y, b.z, b.w, sr, cr);
-        ff_mac(ax.x, ax.y, b.z, b.w, si, ci);
-        ff_mac(-ay.x, -ay.y, b.x, b.y, si, ci);
+        ff_mac(a.xh, a.xl, b.xh, b.xl, sr, cr);
+        ff_mac(a.yh, a.yl, b.yh, b.yl, sr, cr);
+        ff_mac(a.xh, a.xl, b.yh, b.yl, si, ci);
+        ff_mac(-a.yh, -a.yl, b.xh, b.xl, si, ci);
     }
-    __device__ __forceinline__ void add(dd2 a, dd2 b) { add(a, pre(b)); }
-    __device__ __forceinline__ void add_norm(dd2 a)
+    __device__ __forceinline__ void add_norm(ffc a)
     {
-        const float2 ax = dsplit(a.x), ay = dsplit(a.y);
-        ff_mac(ax.x, ax.y, ax.x, ax.y, sr, cr);
-        ff_mac(ay.x, ay.y, ay.x, ay.y, sr, cr);
+        ff_mac(a.xh, a.xl, a.xh, a.xl, sr, cr);
+        ff_mac(a.yh, a.yl, a.yh, a.yl, sr, cr);
     }
     __device__ __forceinline__ double2 value() const { return make_double2(ff2d(sr, cr), ff2d(si, ci)); }
     __device__ __forceinline__ double2 warp_value() const
@@ -380,7 +389,7 @@ struct DotAccDD {
 template <class V> struct DotAcc;
 template <> struct DotAcc<double2> : DotAccD {};
 template <> struct DotAcc<float2> : DotAccF {};
-template <> struct DotAcc<dd2> : DotAccDD {};
+template <> struct DotAcc<ffc> : DotAccFF {};
 
 __device__ __forceinline__ double2 warp_sum(double2 v)
 {

@@ -31,7 +31,7 @@ uint64_t binom_host(int n, int k)
     return r;
 }
 
-size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(double2); }   // (dd2 = double2)
+size_t elem_size(int dtype) { return dtype == KRY_C64 ? sizeof(float2) : sizeof(double2); }   // (sizeof(ffc) = 16)
 
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -131,7 +131,7 @@ int grid_for(const kry_ham_s *H, int dtype, int *gridH, int *gridB)
     const int rl = rl_in_smem(b);
     const int hvf = H->shape[dtype_slot(dtype)][1];
     const int g = dtype == KRY_C64    ? vector_grid<float2>(b, rl, hvf, gridH, gridB)
-                  : dtype == KRY_C128E ? vector_grid<dd2>(b, rl, hvf, gridH, gridB)
+                  : dtype == KRY_C128E ? vector_grid<ffc>(b, rl, hvf, gridH, gridB)
                                        : vector_grid<double2>(b, rl, hvf, gridH, gridB);
     const int ov = H->shape[dtype_slot(dtype)][0];
     if (g > 0 && ov > 0) *gridB = ov;
@@ -146,11 +146,16 @@ void drop_graph(kry_ham_s *H)
     H->prof_ev.clear();
 }
 
-// kernel kind of the k-th launch in the captured step (3 per Lanczos index, then 2)
+// Profile intervals of the captured step: four per Lanczos index (the H.v, pass A's dots,
+// pass B, pass C), then the small exponential and the combine; kind of the k-th interval.
+int n_intervals(int m) { return 4 * m + 2; }
 int kind_of(int k, int m)
 {
-    if (k < 3 * m) return k % 3;   // pass A, pass B, pass C
-    return k == 3 * m ? KIND_EXP : KIND_COMBINE;
+    if (k < 4 * m) {
+        const int q = k % 4;
+        return q == 0 ? KIND_HV : q == 1 ? KIND_PASSA : q == 2 ? KIND_PASSB : KIND_PASSC;
+    }
+    return k == 4 * m ? KIND_EXP : KIND_COMBINE;
 }
 
 template <class V>
@@ -159,9 +164,8 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
-    const int nk = 3 * m + 2;   // kernels per step
     if (H->prof_on) {
-        H->prof_ev.resize(nk + 1);
+        H->prof_ev.resize(n_intervals(m) + 1);
         for (auto &e : H->prof_ev) KRY_CU(cudaEventCreate(&e));
     }
     KRY_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -185,6 +189,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
         mark();
         rc = launch_hv<V>(a, jj, gridH, cs, after_cond ? 0 : 1);
+        mark();
         if (rc == KRY_OK) rc = launch_dots<V>(a, 0, jj, grid, cs);
         mark();
         if (H->plain_graph) {
@@ -235,7 +240,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     }
     mark();
     if (rc == KRY_OK) rc = launch_smallexp(ea, cs, after_cond ? 0 : 1);
-    if constexpr (!std::is_same<V, dd2>::value) {
+    if constexpr (!std::is_same<V, ffc>::value) {
     if (rc == KRY_OK && opt && opt->vec_out) {
         VecOutArgs<V> va{};
         va.W = a.W;
@@ -250,7 +255,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
     }   // (the vector outputs of the adjoint are complex128 or complex64 only)
     mark();
     if (rc == KRY_OK) rc = launch_lincomb<V>(a, 2, 0, gridB, cs);
-    if constexpr (!std::is_same<V, dd2>::value) {
+    if constexpr (!std::is_same<V, ffc>::value) {
         if (rc == KRY_OK && opt && opt->ckpt)
             rc = launch_ckpt<V>(a.W, (V *)opt->ckpt, opt->ldC, a.ctl, a.b.D, gridB, cs);
     }
@@ -300,6 +305,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     ea.W = a.W;
     ea.ldW = l.ldW;
     ea.c64 = dtype == KRY_C64;
+    ea.ff = std::is_same<V, ffc>::value;
     ea.Yout = (opt && opt->vec_out) ? (double2 *)(base + l.oY) : nullptr;
     const int want_C = (opt && opt->C_out) ? 1 : 0;
     if (want_C) {
@@ -368,20 +374,25 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     }
     KRY_CU(cudaMemcpyAsync(a.ctl, &c, sizeof c, cudaMemcpyHostToDevice, s));
     KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
+    constexpr bool FF = std::is_same<V, ffc>::value;   // complex128 in and out, float-float inside
     if (general) {
-        KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        if (FF) {
+            if (int rc = launch_c128_to_ffc(d_psi0, (void *)a.G, nvec, s)) return rc;
+        } else {
+            KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        }
         if (int rc = launch_lincomb<V>(a, 3, 0, gridB, s)) return rc;
     } else {
         KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
-        if (int rc = launch_set_basis_state(a.W, dtype == KRY_C64, (uint32_t)c.r0, s)) return rc;
+        if (int rc = launch_set_basis_state(a.W, dtype == KRY_C64, (uint32_t)c.r0, s, FF)) return rc;
     }
     // replay until the device reports the last output time
     KryCtl *hp = (KryCtl *)H->h_poll;
     long long launched = 0;
     const long long max_launch = 500000;   // Krylov steps before KRY_ETIMEOUT
     int batch = 1;
-    const int nk = 3 * m + 2;
-    const double vp0[5] = {0, 0, 0, 0, 0};
+    const int nk = 3 * m + 2;   // kernels of the step graph (pass C not counted)
+    const double vp0[NKIND] = {0, 0, 0, 0, 0, 0};
     for (;;) {
         if (H->prof_on) batch = 1;   // events are read after every step
         for (int i = 0; i < batch; ++i) KRY_CU(cudaGraphLaunch(H->gexec, s));
@@ -389,7 +400,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         KRY_CU(cudaMemcpyAsync(hp, a.ctl, sizeof(KryCtl), cudaMemcpyDeviceToHost, s));
         KRY_CU(cudaStreamSynchronize(s));
         if (H->prof_on) {
-            for (int k = 0; k < nk; ++k) {
+            for (int k = 0; k < n_intervals(m); ++k) {
                 float ms = 0.f;
                 KRY_CU(cudaEventElapsedTime(&ms, H->prof_ev[k], H->prof_ev[k + 1]));
                 H->prof_ms[kind_of(k, m)] += ms;
@@ -417,7 +428,11 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     }
     KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * H->K, cudaMemcpyDeviceToHost, s));
     if (want_C) KRY_CU(cudaMemcpyAsync(opt->C_out, ea.C, sizeof(double) * n_times, cudaMemcpyDeviceToHost, s));
-    if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    if (d_psi_out && FF) {
+        if (int rc = launch_ffc_to_c128(a.W, d_psi_out, nvec, s)) return rc;
+    } else if (d_psi_out) {
+        KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    }
     KRY_CU(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
@@ -489,17 +504,16 @@ int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
 }
 
 // One Krylov step of the batched path, in groups whose boundaries carry the profile events:
-// per Lanczos index {pass A, reduce}, {pass B, reduce}, {pass C1, reduce, pass C2, reduce,
-// m_run}; then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
+// per Lanczos index {H.v}, {pass A's dots, reduce}, {pass B, reduce}, {pass C1, reduce,
+// pass C2, reduce, m_run}; then {exp scan, exp apply} and {combine, reduce, step bookkeeping}.
 template <class V>
 int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m, int grid, int gridB,
                    int general)
 {
     cudaStream_t cs = H->cap_stream;
     cudaGraph_t g = nullptr;
-    const int nk = 3 * m + 2;
     if (H->prof_on) {
-        H->prof_ev.resize(nk + 1);
+        H->prof_ev.resize(n_intervals(m) + 1);
         for (auto &e : H->prof_ev) KRY_CU(cudaEventCreate(&e));
     }
     KRY_CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -514,7 +528,9 @@ int capture_step_b(kry_ham_s *H, const EvArgsB<V> &a, const ExpArgsB &ea, int m,
     const double2 *part = a.part;
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
         mark();
-        rc = launch_passA_b<V>(a, jj, grid, cs);
+        rc = launch_passA_b<V>(a, jj, grid, cs, 1);
+        mark();
+        if (rc == KRY_OK) rc = launch_passA_b<V>(a, jj, grid, cs, 2);
         if (rc == KRY_OK) rc = launch_reduce_b(a.ctl, part, grid, a.K, a.Kp, 0, jj, general, 0, cs);
         mark();
         if (rc == KRY_OK) rc = launch_lincomb_b<V>(a, 0, jj, gridB, cs);
@@ -653,7 +669,6 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     KryHdrB *hp = (KryHdrB *)H->h_poll;
     long long launched = 0;
     const long long max_launch = 500000;   // Krylov steps before KRY_ETIMEOUT
-    const int nk = 3 * m + 2;
     int batch = 1;
     for (;;) {
         if (H->prof_on) batch = 1;
@@ -662,7 +677,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         KRY_CU(cudaMemcpyAsync(hp, &a.ctl->hd, sizeof(KryHdrB), cudaMemcpyDeviceToHost, s));
         KRY_CU(cudaStreamSynchronize(s));
         if (H->prof_on) {
-            for (int k = 0; k < nk; ++k) {
+            for (int k = 0; k < n_intervals(m); ++k) {
                 float ms = 0.f;
                 KRY_CU(cudaEventElapsedTime(&ms, H->prof_ev[k], H->prof_ev[k + 1]));
                 H->prof_ms[kind_of(k, m)] += ms;
@@ -817,7 +832,7 @@ extern "C" int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double
     if (!d_psi0) { set_error("kry_evolve: d_psi0 is NULL"); return KRY_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C128E)
-        return evolve_t<dd2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+        return evolve_t<ffc>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
@@ -839,7 +854,7 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C128E)
-        return evolve_t<dd2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+        return evolve_t<ffc>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
@@ -878,7 +893,7 @@ int evolve_states(kry_ham H, int dtype, const uint64_t *states, const double *ti
     EvOpts opt;
     opt.C_out = C_out;
     if (dtype == KRY_C128E)
-        return evolve_t<dd2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats, s,
+        return evolve_t<ffc>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats, s,
                              &opt);
     return dtype == KRY_C64
                ? evolve_t<float2>(H, dtype, nullptr, states[0], false, times, n_times, m, tol, nullptr, P_out, stats,

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(32) k_smallexp(ExpArgs ea)
             const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->r0;
             double2 w;
             if (ea.c64) { float2 f = ((const float2 *)ea.W)[idx]; w = make_double2(f.x, f.y); }
+            else if (ea.ff) { float4 f = ((const float4 *)ea.W)[idx]; w = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w); }
             else w = ((const double2 *)ea.W)[idx];
             // <psi0|v_j> with psi0 = e_{r0}: the (real-valued psi0) conjugate is trivial
             const double s = ctl->sigma[lane];

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
     KryCtl *ctl = a.ctl;
     if (ctl->done || jj >= ctl->m_eff) return;
     if (MODE == 1 && !ctl->corr) return;
-    constexpr bool DD = std::is_same<V, dd2>::value;   // FP64 storage, float-float arithmetic
+    constexpr bool DD = std::is_same<V, ffc>::value;   // float-float vectors
     constexpr bool F32 = std::is_same<V, float2>::value;
     constexpr int KC = (F32 || DD) ? 32 : 64;          // columns (rows in flight per vector)
     constexpr int RT = DD ? 4 : 8;                      // rows per column and tile
@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
         ctl->normu2 = fin[SLOT_NRM].x;
         ctl->n_hv += 1;
         ctl->vec_passes += (double)(jj + 4);
-        ctl->vp_kind[0] += (double)(jj + 4);
+        ctl->vp_kind[KIND_PASSA] += (double)(jj + 2);   // u and v_0 .. v_j
+        ctl->vp_kind[KIND_HV] += 2.0;                  // the H.v: v_j read, u written
         ctl->counter = 0;
         return;
     }
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
     if (nw2 > 0.0) ctl->max_orth = fmax(ctl->max_orth, sqrt(nd2 / nw2));
     ctl->n_c1 += 1;
     ctl->vec_passes += (double)(jj + 2);
-    ctl->vp_kind[2] += (double)(jj + 2);
+    ctl->vp_kind[KIND_PASSC] += (double)(jj + 2);
     ctl->corr = 0;
     if (nw2 > 0.0 && sqrt(nd2) > ctl->eta_corr * sqrt(nw2)) {
         ctl->corr2 = 1;
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
     const double2 gdot = fin[SLOT_G];
     if (MODE == 0) {
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
-        ctl->vp_kind[1] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        ctl->vp_kind[KIND_PASSB] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         // One classical Gram-Schmidt pass is enough unless the projection cancelled most of
         // u (||w|| < eta ||u||, the Daniel-Gragg-Kaufman-Stewart test), or the lengths show a
         // loss of orthogonality: with c = V^H u and G = V^H V = I + E, ||w||^2 = ||u||^2 -
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
     } else if (MODE == 1) {
         ctl->n_corr += 1;
         ctl->vec_passes += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
-        ctl->vp_kind[2] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
+        ctl->vp_kind[KIND_PASSC] += (double)(jj + 3) + (a.G ? 1.0 : 0.0);
         ctl->corr2 = 0;
         finalize_beta(ctl, jj, nw2, gdot);
     } else {
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
                                     : make_double2(gdot.x / b0, gdot.y / b0);
         }
         ctl->vec_passes += (double)(nvec + 1) + ((a.G && MODE == 2) ? 1.0 : 0.0);
-        if (MODE == 2) ctl->vp_kind[4] += (double)(nvec + 1) + (a.G ? 1.0 : 0.0);
+        if (MODE == 2) ctl->vp_kind[KIND_COMBINE] += (double)(nvec + 1) + (a.G ? 1.0 : 0.0);
         ctl->m_eff = ctl->m;
         ctl->corr = 0;
         ctl->corr2 = 0;
@@ -522,6 +523,8 @@ __global__ void k_set_basis_state(V *W0, uint32_t r0)
     one.x = 1;
     W0[r0] = one;
 }
+
+__global__ void k_set_basis_state_ff(ffc *W0, uint32_t r0) { W0[r0] = ffc{1.f, 0.f, 0.f, 0.f}; }
 
 // ---------------------------------------------------------------- dense vector output
 
@@ -715,7 +718,7 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
         return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
     };
     *gridH = fit(occH);
-    if constexpr (!std::is_same<V, dd2>::value) {
+    if constexpr (!std::is_same<V, ffc>::value) {
         if (b.list) {
             if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
         }
@@ -727,7 +730,7 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
 template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
-    if constexpr (!std::is_same<V, dd2>::value) {
+    if constexpr (!std::is_same<V, ffc>::value) {
         if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
     }
     EvArgs<V> ah = a;
@@ -764,10 +767,43 @@ int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t 
     return KRY_OK;
 }
 
-int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s)
+int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s, int ff)
 {
     if (c64) k_set_basis_state<float2><<<1, 1, 0, s>>>((float2 *)W0, r0);
+    else if (ff) k_set_basis_state_ff<<<1, 1, 0, s>>>((ffc *)W0, r0);
     else k_set_basis_state<double2><<<1, 1, 0, s>>>((double2 *)W0, r0);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+
+// complex128 <-> float-float vectors (dtype KRY_C128E): in at the initial vector, out at psi(t)
+__global__ void __launch_bounds__(NTHR) k_c128_to_ffc(const double2 *__restrict__ src, ffc *__restrict__ dst, size_t n)
+{
+    for (size_t r = (size_t)blockIdx.x * NTHR + threadIdx.x; r < n; r += (size_t)gridDim.x * NTHR)
+        dst[r] = VT<ffc>::from(__ldg(src + r));
+}
+__global__ void __launch_bounds__(NTHR) k_ffc_to_c128(const ffc *__restrict__ src, double2 *__restrict__ dst, size_t n)
+{
+    for (size_t r = (size_t)blockIdx.x * NTHR + threadIdx.x; r < n; r += (size_t)gridDim.x * NTHR) {
+        const ffc v = ldg(src + r);
+        dst[r] = make_double2(ff2d(v.xh, v.xl), ff2d(v.yh, v.yl));
+    }
+}
+static unsigned convert_grid(size_t n)
+{
+    return (unsigned)std::max<size_t>(1, std::min<size_t>((n + NTHR - 1) / NTHR, (size_t)sm_count() * 8));
+}
+int launch_c128_to_ffc(const void *src, void *dst, size_t n, cudaStream_t s)
+{
+    if (n == 0) return KRY_OK;
+    k_c128_to_ffc<<<convert_grid(n), NTHR, 0, s>>>((const double2 *)src, (ffc *)dst, n);
+    KRY_CU(cudaGetLastError());
+    return KRY_OK;
+}
+int launch_ffc_to_c128(const void *src, void *dst, size_t n, cudaStream_t s)
+{
+    if (n == 0) return KRY_OK;
+    k_ffc_to_c128<<<convert_grid(n), NTHR, 0, s>>>((const ffc *)src, (double2 *)dst, n);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
@@ -815,15 +851,15 @@ int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, 
 
 template int launch_dots<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
 template int launch_dots<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
-template int launch_dots<dd2>(const EvArgs<dd2> &, int, int, int, cudaStream_t, int);
+template int launch_dots<ffc>(const EvArgs<ffc> &, int, int, int, cudaStream_t, int);
 template int vector_grid<double2>(const DevBasis &, int, int, int *, int *);
 template int vector_grid<float2>(const DevBasis &, int, int, int *, int *);
-template int vector_grid<dd2>(const DevBasis &, int, int, int *, int *);
+template int vector_grid<ffc>(const DevBasis &, int, int, int *, int *);
 template int launch_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);
 template int launch_hv<float2>(const EvArgs<float2> &, int, int, cudaStream_t, int);
-template int launch_hv<dd2>(const EvArgs<dd2> &, int, int, cudaStream_t, int);
+template int launch_hv<ffc>(const EvArgs<ffc> &, int, int, cudaStream_t, int);
 template int launch_lincomb<double2>(const EvArgs<double2> &, int, int, int, cudaStream_t, int);
 template int launch_lincomb<float2>(const EvArgs<float2> &, int, int, int, cudaStream_t, int);
-template int launch_lincomb<dd2>(const EvArgs<dd2> &, int, int, int, cudaStream_t, int);
+template int launch_lincomb<ffc>(const EvArgs<ffc> &, int, int, int, cudaStream_t, int);
 
 }  // namespace kry

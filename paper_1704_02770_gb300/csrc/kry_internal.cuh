@@ -12,10 +12,12 @@
 
 namespace kry {
 
-// A complex number stored in FP64 (the layout of double2) on which the vector kernels do
-// double-float arithmetic on the FP32 pipe (dtype KRY_C128E; see kry_device.cuh).
-struct __align__(16) dd2 {
-    double x, y;
+// A complex number as two float-float numbers, x = xh + xl and y = yh + yl (about 48
+// significant bits each, 16 bytes like complex128): the Krylov vectors of dtype KRY_C128E,
+// on which the vector kernels do float-float arithmetic on the FP32 pipe (kry_device.cuh).
+// Inputs and outputs of that dtype stay complex128; they are converted at the boundary.
+struct __align__(16) ffc {
+    float xh, xl, yh, yl;
 };
 
 // Index of a dtype's launch shape: KRY_C128, KRY_C64, KRY_C128E.
@@ -116,13 +118,18 @@ constexpr int KBMAX = 128;   // largest K of one batched evolution
 constexpr int PSB = 36;      // partial-sum slots per (CTA, realisation): dots, then NRM, G
 constexpr int TROWS = 16;    // rows (states) per CTA tile of the batched kernels
 
+// kernel kinds of the profile: pass A's dots (with alpha_j and ||u||^2), pass B (the Lanczos
+// update), pass C (the second Gram-Schmidt pass), the small exponential, the combine, and
+// pass A's H.v
+enum { KIND_PASSA = 0, KIND_PASSB = 1, KIND_PASSC = 2, KIND_EXP = 3, KIND_COMBINE = 4, KIND_HV = 5, NKIND = 6 };
+
 // Control block of a batched evolution: one Lanczos recurrence per realisation k
 // (structure of arrays, k fastest), one shared time grid and step size.
 struct KryHdrB {   // shared scalars (copied to the host when polling)
     double t_now, t_end, tol, t_next;
     double eta_corr, eta_bd;
     double err_sum, max_orth, vec_passes;
-    double vp_kind[5];
+    double vp_kind[NKIND];
     unsigned long long n_hv, n_steps, n_corr, n_bd;
     int K, m, m_run, corr_any, finishing, done, err;
     int n_times, next_out, next_out_new, r0;
@@ -171,7 +178,8 @@ struct ExpArgsB {
     const double *glx, *glw;   // Gauss-Legendre nodes and weights on [-1, 1] (with C)
 };
 
-template <class V> int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s);
+// pass A of the batched path: part 0 = the H.v and the dots, 1 = the H.v only, 2 = the dots only
+template <class V> int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s, int part = 0);
 template <class V> int launch_lincomb_b(const EvArgsB<V> &a, int mode, int jj, int grid, cudaStream_t s);
 int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, int mode, int jj,
                     int general, double es_bytes_per_vec, cudaStream_t s);
@@ -194,7 +202,7 @@ struct KryCtl {
     double t_now, t_end, tol, tau_prev;
     double eta_corr, eta_bd;   // second-pass and breakdown thresholds (relative)
     double err_sum, max_orth, vec_passes;
-    double vp_kind[5];         // vector passes by kernel kind (pass A, B, C, -, combine)
+    double vp_kind[NKIND];     // vector passes by kernel kind (KIND_*)
     long long n_hv, n_steps, n_corr, n_bd;
     int m, m_eff, corr, finishing, done, err;
     int n_times, next_out, r0;
@@ -255,9 +263,10 @@ struct ExpArgs {
     KryCtl *ctl;
     const double *times;
     double *P;
-    const void *W;   // Krylov vectors (element type given by c64)
+    const void *W;   // Krylov vectors (element type given by c64 and ff)
     size_t ldW;
     int c64;
+    int ff;          // the vectors are float-float (ffc)
     double2 *Yout;   // nullable: combine coefficients of every output time [n_times][MMAX]
     double *C;       // nullable: temporal autocorrelation C(t_o) of every output time
     const double *glx, *glw;   // NGL-point Gauss-Legendre nodes and weights on [-1, 1] (with C)
@@ -284,12 +293,13 @@ template <class V> int launch_lincomb(const EvArgs<V> &a, int mode, int jj, int 
                                       cudaStream_t s, int pdl = 1);
 template <class V> int launch_dots(const EvArgs<V> &a, int mode, int jj, int grid, cudaStream_t s, int pdl = 1);
 template <class V> int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gridB);
-int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s);
+int launch_set_basis_state(void *W0, int c64, uint32_t r0, cudaStream_t s, int ff = 0);
+// complex128 <-> float-float vectors of n elements (the boundary of KRY_C128E)
+int launch_c128_to_ffc(const void *src, void *dst, size_t n, cudaStream_t s);
+int launch_ffc_to_c128(const void *src, void *dst, size_t n, cudaStream_t s);
 // small exponential (kry_exp.cu)
 int launch_smallexp(const ExpArgs &a, cudaStream_t s, int pdl = 1);
 
-// kernel kinds of the profile
-enum { KIND_PASSA = 0, KIND_PASSB = 1, KIND_PASSC = 2, KIND_EXP = 3, KIND_COMBINE = 4, NKIND = 5 };
 
 }  // namespace kry
 
@@ -338,8 +348,8 @@ struct kry_ham_s {
     // profiling: CUDA events recorded between the kernels of the captured step
     int prof_on;
     std::vector<cudaEvent_t> prof_ev;
-    double prof_ms[5], prof_bytes[5];
-    int64_t prof_launches[5];
+    double prof_ms[kry::NKIND], prof_bytes[kry::NKIND];
+    int64_t prof_launches[kry::NKIND];
 };
 
 // Launch shape of a new Hamiltonian: the occupancy-rule grid, prefetching dots, two update

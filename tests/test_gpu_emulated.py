@@ -1,7 +1,8 @@
-"""KRY_C128E: complex128 storage with the vector arithmetic (H.v sums, dots, updates) in
-float-float on the FP32 pipe, against the oracle at the FP64 bar (|dP| <= 1e-10) and against
-the FP64-arithmetic form.  The arithmetic carries about 47 significant bits, so its results
-differ from the FP64 form's by rounding at the 1e-13 level, far inside the bar.
+"""KRY_C128E: complex128 in and out, float-float Krylov vectors and vector arithmetic (H.v
+sums, dots, updates) on the FP32 pipe inside, against the oracle at the FP64 bar (|dP| <=
+1e-10) and against the FP64-arithmetic form.  Storage and arithmetic carry about 47-48
+significant bits, so its results differ from the FP64 form's by rounding at the 1e-13 level,
+far inside the bar.
 """
 import itertools
 

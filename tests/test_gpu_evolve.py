@@ -164,14 +164,17 @@ def test_profiling_changes_nothing_and_counts_every_kernel(kry):
     m = 30
     steps = prof["smallexp"]["launches"]
     assert steps >= st1["n_krylov_steps"]
-    for k in ("passA", "passB", "passC"):
+    for k in ("hv", "dots", "update", "passC"):
         assert prof[k]["launches"] == m * steps
-    assert prof["passA"]["ms"] > 0.0 and prof["passB"]["ms"] > 0.0 and prof["passC"]["ms"] >= 0.0
+    assert min(prof[k]["ms"] for k in ("hv", "dots", "update")) > 0.0 and prof["passC"]["ms"] >= 0.0
     assert prof["combine"]["launches"] == steps
-    # algorithmic bytes of pass A: H.v reads v_j and writes u (2 vectors); the dots read
-    # u and v_0..v_j (j + 2 vectors); all complex128 of length D
-    want = st1["n_krylov_steps"] * sum(j + 4 for j in range(m)) * B.dim * 16
-    assert prof["passA"]["bytes"] == pytest.approx(want, rel=1e-12)
+    # algorithmic bytes: the H.v reads v_j and writes u (2 vectors); the dots read u and
+    # v_0..v_j (j + 2 vectors); the update reads u and v_0..v_j and writes w (j + 3); all
+    # complex128 of length D
+    n, vec = st1["n_krylov_steps"], B.dim * 16
+    assert prof["hv"]["bytes"] == pytest.approx(n * 2 * m * vec, rel=1e-12)
+    assert prof["dots"]["bytes"] == pytest.approx(n * sum(j + 2 for j in range(m)) * vec, rel=1e-12)
+    assert prof["update"]["bytes"] == pytest.approx(n * sum(j + 3 for j in range(m)) * vec, rel=1e-12)
     # three kernels per Lanczos index (H.v, dots, update), then exponential and combine; the
     # second Gram-Schmidt pass (two kernels) only where a conditional node runs it
     assert st1["n_launches"] == steps * (3 * m + 2) + 2 * st1["n_second_dots"] + 1
