@@ -212,9 +212,10 @@ int kry_tridiag_expv_noalloc(const double *alpha, const double *beta, int m, dou
  * record CUDA events between the kernels of every Krylov step (on the caller's stream,
  * inside the replayed graph) and synchronise after each step; 0 turns it off.  With 2 no
  * events are recorded, and the step graph launches the second Gram-Schmidt pass as two plain
- * kernels in every Lanczos index (returning at once unless needed) instead of through a
- * conditional node: external profilers such as Nsight Compute cannot see the kernels of a
- * graph that has conditional nodes.  KRY_EINVAL for other values.
+ * kernels in every Lanczos index (returning at once unless needed) even where
+ * kry_set_second_pass_node asked for a conditional node: external profilers such as Nsight
+ * Compute cannot see the kernels of a graph that has conditional nodes.  KRY_EINVAL for
+ * other values.
  * kry_profile_read fills, for the six kernel kinds
  *   0 = pass A's dots (<v_i, u> for i <= j, alpha_j and ||u||^2), 1 = pass B (the Lanczos
  *   update w = u - sum c_i v_i and ||w||^2), 2 = pass C (the second Gram-Schmidt pass, when
@@ -274,6 +275,17 @@ int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_pro
  * > 1e-12 (1e-5) ||c|| ||w|| plus the storage-precision noise, a sign that V has lost
  * orthogonality.  Returns KRY_EINVAL for other values of on. */
 int kry_set_orth_check(kry_ham H, int on);
+
+/* Form of the second Gram-Schmidt pass in the captured Krylov step (single-realisation
+ * evolutions; not part of the paper's method).  on = 0 (the default): its two kernels are
+ * launched in every Lanczos index and return at once unless pass B flagged the pass.  on = 1:
+ * they are the body of a conditional graph node (CUDA 12.4+ IF node) whose value pass B's
+ * last CTA sets on the device, so nothing is launched where the pass is not needed.  Both
+ * forms give bitwise the same results.  The kernel after a conditional node cannot start
+ * before the node ends (no programmatic dependent launch across it); on GB300 the
+ * conditional form measured 0.7-2.1% slower over whole L = 24 evolutions, hence the default.
+ * KRY_EINVAL unless on is 0 or 1. */
+int kry_set_second_pass_node(kry_ham H, int on);
 
 /* Bytes of device workspace an evolution of H (single or batched by H's K) needs in dtype
  * with Krylov dimension m and n_times output times, at the current launch shape (an autotuned

@@ -68,6 +68,7 @@ SIGNATURES = {
     "kry_set_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "kry_get_shape": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "kry_set_orth_check": (_i, [_vp, _i]),
+    "kry_set_second_pass_node": (_i, [_vp, _i]),
     "kry_profile_enable": (_i, [_vp, _i]),
     "kry_profile_read": (_i, [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "kry_measure_peaks": (_i, [_dp, _dp, _vp]),
@@ -310,6 +311,12 @@ class Hamiltonian:
         """Measure (and subtract when needed) <v_i, w> after every Lanczos update; on = 2
         subtracts them after every update (kry_set_orth_check)."""
         _check(load().kry_set_orth_check(self._h, int(on)))
+
+    def second_pass_node(self, on=True):
+        """Launch the second Gram-Schmidt pass through a conditional graph node (True) or as
+        kernels that return at once unless needed (False, the default)
+        (kry_set_second_pass_node)."""
+        _check(load().kry_set_second_pass_node(self._h, int(on)))
 
     def set_grid(self, grid: int, dtype: str = "c128"):
         _check(load().kry_set_grid(self._h, _code(dtype), grid))

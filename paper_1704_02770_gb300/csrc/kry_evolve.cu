@@ -146,6 +146,9 @@ void drop_graph(kry_ham_s *H)
     H->prof_ev.clear();
 }
 
+// pass C launched in every Lanczos index (true) or as a conditional node
+bool plain_step_graph(const kry_ham_s *H) { return H->plain_graph || !H->cond_pass_c; }
+
 // Profile intervals of the captured step: four per Lanczos index (the H.v, pass A's dots,
 // pass B, pass C), then the small exponential and the combine; kind of the k-th interval.
 int n_intervals(int m) { return 4 * m + 2; }
@@ -177,13 +180,16 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         }
         ++k;
     };
-    // The second Gram-Schmidt pass (pass C: its dots, then the subtraction) is the body of a
-    // conditional node after pass B, whose last CTA sets the node's value: the pass costs
-    // nothing in the Lanczos indices where it is not needed.  The kernel after a conditional
-    // node is launched without programmatic dependence (that only links two kernels).
-    // With plain_graph set (for external profilers, which cannot see the kernels of a graph
-    // that has conditional nodes) pass C is launched in every Lanczos index and returns at once
-    // unless flagged.
+    // The second Gram-Schmidt pass (pass C: its dots, then the subtraction) runs only where
+    // pass B flagged it, in one of two forms.  Plain (the default): its two kernels are
+    // launched in every Lanczos index and return at once unless flagged; with programmatic
+    // dependent launch they cost about 3 us each.  Conditional (kry_set_second_pass_node):
+    // they are the body of a conditional node after pass B, whose last CTA sets the node's
+    // value; the kernel after the node is launched without programmatic dependence (that
+    // only links two kernels), and on GB300 this form measured 0.7-2.1% slower over whole
+    // evolutions at L = 24.  kry_profile_enable(H, 2) forces the plain form (external
+    // profilers cannot see the kernels of a graph that has conditional nodes).
+    const bool plain = plain_step_graph(H);
     cudaStream_t cs2 = H->cap_stream2;
     int after_cond = 0;
     for (int jj = 0; jj < m && rc == KRY_OK; ++jj) {
@@ -192,7 +198,7 @@ int capture_step(kry_ham_s *H, const EvArgs<V> &a, const ExpArgs &ea, int m, int
         mark();
         if (rc == KRY_OK) rc = launch_dots<V>(a, 0, jj, grid, cs);
         mark();
-        if (H->plain_graph) {
+        if (plain) {
             if (rc == KRY_OK) rc = launch_lincomb<V>(a, 0, jj, gridB, cs);
             mark();
             if (rc == KRY_OK) rc = launch_dots<V>(a, 1, jj, grid, cs);
@@ -318,7 +324,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     // graph of one Krylov step (reused while the workspace and the shape are unchanged)
     const int skey = shp[1] * 100 + shp[2] * 10 + shp[3];
     if (H->gexec && (H->g_dtype != dtype || H->g_m != m || H->g_general != (int)general || H->g_shape != skey ||
-                     H->g_plain != H->plain_graph ||
+                     H->g_plain != (int)plain_step_graph(H) ||
                      H->g_grid != grid || H->g_gridB != gridB || H->g_gridH != gridH || H->g_ws != H->ws ||
                      H->g_G != (const void *)(base + l.oP) ||
                      H->ws_bytes < l.bytes || (int)H->prof_ev.empty() == H->prof_on ||
@@ -330,7 +336,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         H->g_dtype = dtype; H->g_m = m; H->g_general = general; H->g_grid = grid; H->g_gridB = gridB;
         H->g_gridH = gridH;
         H->g_shape = skey;
-        H->g_plain = H->plain_graph;
+        H->g_plain = plain_step_graph(H);
         H->g_ws = H->ws; H->g_G = base + l.oP;
         H->g_vec = vkey; H->g_ck = ckey; H->g_C = want_C;
         H->g_ldo = opt ? opt->ldOut : 0;
@@ -445,8 +451,9 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->max_orth_loss = hp->max_orth;
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (nk + (H->plain_graph ? 2 * m : 0) + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) +
-                         (H->plain_graph ? 0 : 2 * hp->n_c1) + 1;
+        const bool plain = plain_step_graph(H);
+        st->n_launches = launched * (nk + (plain ? 2 * m : 0) + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) +
+                         (plain ? 0 : 2 * hp->n_c1) + 1;
         st->n_second_dots = hp->n_c1;
     }
     if (opt && opt->ckpt) {
@@ -767,6 +774,13 @@ extern "C" int kry_profile_enable(kry_ham H, int on)
     H->prof_on = on == 1 ? 1 : 0;
     H->plain_graph = on == 2 ? 1 : 0;
     for (int q = 0; q < NKIND; ++q) { H->prof_ms[q] = 0.0; H->prof_bytes[q] = 0.0; H->prof_launches[q] = 0; }
+    return KRY_OK;
+}
+
+extern "C" int kry_set_second_pass_node(kry_ham H, int on)
+{
+    if (!H || on < 0 || on > 1) { set_error("kry_set_second_pass_node: bad arguments (on = 0 or 1)"); return KRY_EINVAL; }
+    H->cond_pass_c = on;
     return KRY_OK;
 }
 

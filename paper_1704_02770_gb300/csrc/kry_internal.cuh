@@ -329,7 +329,8 @@ struct kry_ham_s {
     // cached CUDA graph of one Krylov step
     cudaGraphExec_t gexec;
     int g_dtype, g_m, g_general, g_grid, g_gridB, g_gridH, g_shape, g_plain;
-    int plain_graph;            // pass C as plain launches instead of a conditional node
+    int plain_graph;            // forced plain step graph (kry_profile_enable(H, 2))
+    int cond_pass_c;            // pass C as a conditional node (kry_set_second_pass_node)
     void *g_ws;
     const void *g_G;
     const void *g_vec, *g_ck;   // optional vector-output and checkpoint buffers baked in the graph

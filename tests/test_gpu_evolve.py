@@ -175,9 +175,20 @@ def test_profiling_changes_nothing_and_counts_every_kernel(kry):
     assert prof["hv"]["bytes"] == pytest.approx(n * 2 * m * vec, rel=1e-12)
     assert prof["dots"]["bytes"] == pytest.approx(n * sum(j + 2 for j in range(m)) * vec, rel=1e-12)
     assert prof["update"]["bytes"] == pytest.approx(n * sum(j + 3 for j in range(m)) * vec, rel=1e-12)
-    # three kernels per Lanczos index (H.v, dots, update), then exponential and combine; the
-    # second Gram-Schmidt pass (two kernels) only where a conditional node runs it
-    assert st1["n_launches"] == steps * (3 * m + 2) + 2 * st1["n_second_dots"] + 1
+    # three kernels per Lanczos index (H.v, dots, update) and the two of the second
+    # Gram-Schmidt pass (no-ops unless flagged), then exponential and combine
+    assert st1["n_launches"] == steps * (5 * m + 2) + 1
+    # as a conditional node, the second pass launches only where it runs: the same bits
+    H.second_pass_node(True)
+    H.profile(True)
+    P2, st2 = H.return_probability(c["state"], c["times"][:25], tol=1e-10)
+    steps2 = H.profile_read()["smallexp"]["launches"]
+    H.profile(False)
+    H.second_pass_node(False)
+    assert np.array_equal(P2, P0)
+    assert st2["n_launches"] == steps2 * (3 * m + 2) + 2 * st2["n_second_dots"] + 1
+    with pytest.raises(kry.KryError):
+        H.second_pass_node(2)
 
 
 @pytest.mark.parametrize("dtype,bound", [("c128", 1e-12), ("c64", 1e-5)])
@@ -199,14 +210,16 @@ def test_orthogonality_check(kry, dtype, bound):
     assert np.max(np.abs(P1 - P0)) <= (1e-12 if dtype == "c128" else 1e-6)
 
 
+@pytest.mark.parametrize("node", [False, True])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_second_pass_on_every_vector(kry, dtype):
-    """orth_check(2): the second Gram-Schmidt pass (the conditional node's two kernels) runs and
-    subtracts after every update; the results equal the single-pass run to rounding, and the
-    L16 evolution still matches the oracle."""
+def test_second_pass_on_every_vector(kry, dtype, node):
+    """orth_check(2): the second Gram-Schmidt pass (plain launches, or a conditional node's
+    body) runs and subtracts after every update; the results equal the single-pass run to
+    rounding, and the L16 evolution still matches the oracle."""
     c = workloads.config("L16_fp64")
     B = kry.Basis(c["L"], c["n_up"])
     H = kry.Hamiltonian(B, 1.0, 1.0, c["h"][0])
+    H.second_pass_node(node)
     tol = 1e-10 if dtype == "c128" else 1e-7
     P0, st0 = H.return_probability(c["state"], c["times"], tol=tol, dtype=dtype)
     H.orth_check(2)

@@ -58,6 +58,23 @@ def test_hv_forms_equal_bitwise_on_apply_sizes(kry):
         assert all(np.array_equal(out[0], o) for o in out[1:])
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128e"])
+def test_dots_forms_equal_bitwise_on_apply_sizes(kry, dtype):
+    """The dots with the next vector prefetched into registers and without prefetch, at L = 22
+    and 24 over several Krylov steps to t = 8 (every Lanczos index, so every split of the
+    vectors over the groups, and a ragged last tile): P bitwise equal."""
+    for L in (22, 24):
+        B = kry.Basis(L, L // 2)
+        H = kry.Hamiltonian(B, 1.0, 1.0, workloads.quasiperiodic_field(L, 1.5, 0.2))
+        out = []
+        for dots in (0, 1):
+            H.set_shape([0, 0, dots, 2, 0], dtype)
+            P, st = H.return_probability(workloads.neel_state(L), [0.05, 0.3, 1.0, 4.0, 8.0], tol=1e-7, dtype=dtype)
+            out.append(P)
+        assert st["n_krylov_steps"] >= 2
+        assert all(np.array_equal(out[0], o) for o in out[1:])
+
+
 def test_autotune_single(kry, tmp_path):
     c = workloads.config("L16_fp64")
     B = kry.Basis(c["L"], c["n_up"])
