@@ -525,6 +525,7 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
            "timing": "one evolution per case after a capture run to t=0.1; per-kind times from event "
                      "nodes in the same run"}
     launches = 0
+    Ps = {}
     cases = ([("L30_qp", "c64")] if not full else
              [(n, d) for n in ("L30_clean", "L30_qp") for d in ("c64", "c128", "c128e")])
     B = None
@@ -555,9 +556,10 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
         H.profile(False)
         u, s = aggregate(D * st["n_hv"], sec, world)
         launches += st["n_launches"]
+        Ps[(name, dt)] = np.asarray(P, dtype=np.float64)
         line = {"dtype": dt, "tol": tol, "value": u / s, "unit": "state-updates/s", "ms_per_step": 1e3 * s,
-                "krylov_steps": st["n_krylov_steps"], "hv": st["n_hv"], "P_first": float(P[0]),
-                "P_last": float(P[-1]),
+                "krylov_steps": st["n_krylov_steps"], "hv": st["n_hv"], "second_passes": st["n_second_pass"],
+                "P_first": float(P[0]), "P_last": float(P[-1]),
                 "roofline": roofline(prof, dt, D, c, c["L"], c["n_up"], clocks, traffic_key="l30_")}
         res[f"{name}_{dt}"] = line
         if full and name == "L30_qp" and dt == "c64":
@@ -589,6 +591,7 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
                 if a and b:
                     b["speedup_vs_fp64"] = b["value"] / a["value"]
                     b["time_to_solution_speedup_vs_fp64"] = a["ms_per_step"] / b["ms_per_step"]
+                    b["max_abs_dP_vs_fp64_40_times"] = float(np.max(np.abs(Ps[(name, dt)] - Ps[(name, "c128")])))
     res["_launches"] = launches
     return res
 

@@ -232,7 +232,7 @@ int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *launches);
  * dtype, five ints:
  *   shape[0] CTAs of the streaming kernels: 0 = the occupancy rule (whole SMs times the
  *            resident CTAs of each kernel), else that many CTAs;
- *   shape[1] form of the H.v, two bits: bit 0 set = the targets of up to eight hops computed
+ *   shape[1] form of the H.v, two bits: bit 0 set = the targets of up to four hops computed
  *            first and their loads issued together (else one hop at a time); bit 1 set = the
  *            lower-bit rank table read through the L1 cache instead of staged in shared memory
  *            (at L = 29, 30 that table takes 64 KB of shared memory per CTA);
@@ -267,13 +267,14 @@ int kry_autotune(kry_ham H, int dtype, int m, uint64_t probe_state, double t_pro
  * pass (Sec. 2: Arnoldi orthogonalises each new vector against the whole basis); a second
  * pass is made only when that pass cancelled most of the vector (||w|| < 0.1 ||H v_j||).
  * With on = 1 the dots of every new vector with all previous ones are measured after each
- * pass (kry_stats.max_orth_loss) and subtracted when they exceed 1e-12 ||w|| (complex128) or
- * 1e-5 ||w|| (complex64); with on = 2 they are subtracted after every update (classical
- * Gram-Schmidt applied twice to every vector, as in the oracle).  Besides the cancellation
- * test, the second pass is also taken when the lengths of u = H v_j, of its projections
- * c = V^H u and of w = u - V c disagree with Pythagoras, | ||w||^2 - (||u||^2 - ||c||^2) |
- * > 1e-12 (1e-5) ||c|| ||w|| plus the storage-precision noise, a sign that V has lost
- * orthogonality.  Returns KRY_EINVAL for other values of on. */
+ * pass (kry_stats.max_orth_loss) and subtracted when they exceed eta ||w||, with eta about
+ * 1e4 units of roundoff of the vector storage: 1e-12 (KRY_C128), 3e-11 (KRY_C128E), 1e-5
+ * (KRY_C64); with on = 2 they are subtracted after every update (classical Gram-Schmidt
+ * applied twice to every vector, as in the oracle).  Besides the cancellation test, the
+ * second pass is also taken when the lengths of u = H v_j, of its projections c = V^H u and
+ * of w = u - V c disagree with Pythagoras, | ||w||^2 - (||u||^2 - ||c||^2) | > eta ||c|| ||w||
+ * plus the storage-precision noise, a sign that V has lost orthogonality.  Returns
+ * KRY_EINVAL for other values of on. */
 int kry_set_orth_check(kry_ham H, int on);
 
 /* Form of the second Gram-Schmidt pass in the captured Krylov step (single-realisation

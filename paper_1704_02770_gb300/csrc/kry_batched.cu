@@ -284,6 +284,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
                     }
                 }
             }
+            // fold the float-float compensations back once per tile
+#pragma unroll
+            for (int q = 0; q < QD; ++q)
+                if (g + NG * q <= jj) acc[q].renorm();
+            nrm.renorm();
         }
     }
     double2 *pc = a.part + (size_t)blockIdx.x * PSB * Kp;
@@ -352,6 +357,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
             }
             if (MODE == 4) wtile[rr * Kp + k] = w;
         }
+        nrm.renorm();
+        gacc.renorm();
         if (MODE == 4) {
             __syncthreads();
             if (k < K) {
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
                             vv[rr] = (r0 + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
 #pragma unroll
                         for (int rr = 0; rr < TROWS; ++rr) acc[q].add(vv[rr], wtile[rr * Kp + k]);
+                        acc[q].renorm();
                     }
                 }
             }

@@ -221,10 +221,13 @@ __device__ __forceinline__ void pdl_begin()
 }
 
 // ---------------------------------------------------------------- dot accumulators
-// sum conj(a) b.  complex128: FP64 fused multiply-adds.  complex64: every product is
-// split exactly (p = a*b rounded, e = fma(a, b, -p)) and summed with Knuth's TwoSum into a
-// float pair (s, c), so the accumulation error is of order 2^-48 of the sum of |terms|
-// and the per-thread result is handed on in FP64.
+// sum conj(a) b.  complex128: FP64 fused multiply-adds.  complex64 and float-float: every
+// product is split exactly (p = a*b rounded, e = fma(a, b, -p)) and summed with Knuth's
+// TwoSum into a float pair (s, c): the rounding errors of s are kept exactly, and c gathers
+// them in plain float.  c is folded back into s (renorm, a TwoSum) after every few terms --
+// the callers do it once per tile -- so that its own rounding stays at 2^-48 of |s|: left to
+// grow over the N terms of a thread, c's rounding errors add up to about N 2^-48 of the sum
+// (5e-11 relative at N = 16K, the rows per thread of an L = 30 sector).
 
 __device__ __forceinline__ double2 warp_sum(double2 v);
 
@@ -236,6 +239,7 @@ struct DotAccD {
         im = fma(a.x, b.y, im); im = fma(-a.y, b.x, im);
     }
     __device__ __forceinline__ void add_norm(double2 a) { re = fma(a.x, a.x, re); re = fma(a.y, a.y, re); }
+    __device__ __forceinline__ void renorm() {}
     __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
     // the sum over the warp (valid in every lane)
     __device__ __forceinline__ double2 warp_value() const { return warp_sum(value()); }
@@ -288,6 +292,11 @@ struct DotAccF {
     }
     // |a|^2 (the imaginary part of conj(a) a is zero and is not accumulated)
     __device__ __forceinline__ void add_norm(float2 a) { exact_fma(a.x, a.x, sr, cr); exact_fma(a.y, a.y, sr, cr); }
+    __device__ __forceinline__ void renorm()
+    {
+        ff_renorm(sr, cr);
+        ff_renorm(si, ci);
+    }
     __device__ __forceinline__ double2 value() const
     {
         return make_double2((double)sr + (double)cr, (double)si + (double)ci);
@@ -316,6 +325,14 @@ __device__ __forceinline__ void ff_pair_add(float2 &s, float2 &c, float2 a, floa
     s = t;
     c = __fadd2_rn(c, __fadd2_rn(err, e));
 }
+// (s, c) renormalised by TwoSum, two float-float lanes per instruction
+__device__ __forceinline__ void ff_renorm2(float2 &s, float2 &c)
+{
+    const float2 t = __fadd2_rn(s, c);
+    const float2 z = fsub2(t, s);
+    c = __fadd2_rn(fsub2(s, fsub2(t, z)), fsub2(c, z));
+    s = t;
+}
 struct DotAccF2 {
     float2 s1 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
     float2 s2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
@@ -340,6 +357,11 @@ struct DotAccF2 {
     {
         add(a0, b0);
         add(a1, b1);
+    }
+    __device__ __forceinline__ void renorm()
+    {
+        ff_renorm2(s1, c1);
+        ff_renorm2(s2, c2);
     }
     __device__ __forceinline__ double2 value() const
     {
@@ -375,6 +397,11 @@ struct DotAccFF {
     {
         ff_mac(a.xh, a.xl, a.xh, a.xl, sr, cr);
         ff_mac(a.yh, a.yl, a.yh, a.yl, sr, cr);
+    }
+    __device__ __forceinline__ void renorm()
+    {
+        ff_renorm(sr, cr);
+        ff_renorm(si, ci);
     }
     __device__ __forceinline__ double2 value() const { return make_double2(ff2d(sr, cr), ff2d(si, ci)); }
     __device__ __forceinline__ double2 warp_value() const

@@ -355,7 +355,9 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
     c.t_end = times[n_times - 1];
     c.tol = tol;
     c.n_times = n_times;
-    c.eta_corr = H->orth_check == 2 ? 0.0 : (dtype == KRY_C64 ? 1e-5 : 1e-12);
+    // second-pass threshold on the loss of orthogonality, about 1e4 units of roundoff of the
+    // vector storage: FP64 (2^-53) 1e-12, float-float (2^-48) 3e-11, complex64 (2^-24) 1e-5
+    c.eta_corr = H->orth_check == 2 ? 0.0 : (dtype == KRY_C64 ? 1e-5 : dtype == KRY_C128E ? 3e-11 : 1e-12);
     c.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
     c.eta_cancel = 0.1;
     c.verify = H->orth_check ? 1 : 0;

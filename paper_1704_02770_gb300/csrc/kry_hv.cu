@@ -158,7 +158,7 @@ __device__ __forceinline__ void finalize_beta(KryCtl *ctl, int jj, double nw2, d
 // and nothing else: the gathers of the hops are latency-bound, so as many rows as possible
 // are kept in flight.  alpha_j, ||u||^2 and the dots with the earlier vectors are taken by
 // the streaming pass that follows (k_dots, mode 0).  FORM 0 gathers the hops one by one
-// (hv_row_scaled), FORM 1 in chunks of eight loads in flight (hv_row_chunked); both give the
+// (hv_row_scaled), FORM 1 in rounds of four loads in flight (hv_row_chunked); both give the
 // same bits, the launch shape picks the faster (kry_autotune).
 template <class V, int FORM>
 __global__ void __launch_bounds__(NTHR) k_hv(EvArgs<V> a, int jj)
@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots(EvArgs<V> a, int jj)
                 }
             }
         }
+        // fold the float-float compensations back once per tile
+#pragma unroll
+        for (int q = 0; q < QD; ++q)
+            if (q < nq) acc[q].renorm();
+        nrm.renorm();
     }
     // per warp: the sum over its 32 columns; then the warps of a vector's groups, in order
 #pragma unroll
@@ -452,6 +457,8 @@ __global__ void __launch_bounds__(NTHR, RR == 4 ? 2 : 4) k_lincomb(EvArgs<V> a, 
             nrm.add_norm(wv);
             if (a.G && MODE != 3) gacc.add(ldg(a.G + q[k]), wv);
         }
+        nrm.renorm();
+        gacc.renorm();
     }
     cta_sum_into(nrm, red, SLOT_NRM, wtmp);
     if (a.G) cta_sum_into(gacc, red, SLOT_G, wtmp);

@@ -3,7 +3,7 @@
 // parts, tuned one after another (coordinate descent, each part over its candidates with the
 // others at their best so far):
 //   [0] CTAs of the streaming kernels: the occupancy rule (0) or 1..4 times the SM count;
-//   [1] H.v form: bit 0 = chunks of eight gathers in flight (else one hop at a time), bit 1 =
+//   [1] H.v form: bit 0 = rounds of four gathers in flight (else one hop at a time), bit 1 =
 //       the lower-bit rank table read through L1 (else staged in shared memory);
 //   [2] dots: prefetching the next vector's rows (0) or not (1);
 //   [3] rows per thread of the update pass: 1, 2 or 4;
