@@ -408,7 +408,7 @@ def run_ours(args):
         ue, se_ = aggregate(D * hve, sece, world)
         out["gpu_launches"] += le
         out["fp64_emulated"] = {
-            "dtype": "c128 storage, float-float arithmetic on the FP32 pipe (about 47 bits)",
+            "dtype": "complex128 in and out; float-float vectors and arithmetic on the FP32 pipe (about 48 bits)",
             "value": ue / se_, "unit": "state-updates/s", "ms_per_step": 1e3 * se_ / args.steps,
             "tol": c["tol"], "speedup_vs_fp64": (ue / se_) / value,
             "krylov_steps_per_step": ste["n_krylov_steps"],
