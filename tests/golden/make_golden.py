@@ -12,10 +12,12 @@ the host, far beyond a GPU test's budget, so its results are stored as small tex
                              workload by central differences (step 1e-5) of the oracle's P
   P_L30_<name>_early.txt     P at the first output times of the L = 30 workloads from the
                              moment series of oracle.moments, with its rigorous error bound
+  P_L32_qp_early.txt         the same for the largest sector of the split rank tables, L = 32,
+                             N_up = 16 (D = 601,080,390), h = 1.5 (phi: workloads.phases(5))
 
 Each file's header states the workload, the oracle call, its tolerance and its run time.
 
-    python tests/golden/make_golden.py L24|L22|L20grad|L30 [--jobs N]
+    python tests/golden/make_golden.py L24|L22|L20grad|L30|L32 [--jobs N]
 """
 from __future__ import annotations
 
@@ -177,9 +179,35 @@ def make_L30(jobs: int, hops: int = 12):
                 f.write(f"{t!r} {P!r} {b!r}\n")
 
 
+def make_L32(hops: int = 12):
+    """The largest split-table sector: L = 32, N_up = 16, the quasiperiodic field of the L = 30
+    workload's seed, Neel state; the output times where the series bound is <= 1e-12."""
+    from oracle import moments
+    import workloads
+    L, N = 32, 16
+    h = workloads.quasiperiodic_field(L, 1.5, workloads.phases(5)[0])
+    state = workloads.neel_state(L)
+    t0 = time.time()
+    mu, nball = moments.moments(L, 1.0, 1.0, h, True, state, hops)
+    sec = time.time() - t0
+    with open(os.path.join(HERE, "P_L32_qp_early.txt"), "w") as f:
+        _header(f, ["workload L32_qp: L=32 N_up=16 PBC J=1 Delta=1 h=1.5 (phi: workloads.phases(5)), "
+                    "Neel initial state",
+                    f"oracle: moments.moments over the {nball} states within {hops} hops of psi0 "
+                    f"(moments mu_0..mu_{2 * hops}), moments.return_probability; {sec:.0f} s",
+                    "the output times whose rigorous bound on |P_series - P| is <= 1e-12",
+                    "written by tests/golden/make_golden.py L32",
+                    "columns: t P bound"])
+        for t in workloads.log_times():
+            P, bound = moments.return_probability(mu, t)
+            if bound > 1e-12:
+                break
+            f.write(f"{t!r} {float(P)!r} {float(bound)!r}\n")
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("target", choices=["L24", "L22", "L20grad", "L30"])
+    ap.add_argument("target", choices=["L24", "L22", "L20grad", "L30", "L32"])
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--h", nargs="*", default=None, help="L22: the field amplitudes to run")
     a = ap.parse_args()
@@ -189,5 +217,7 @@ if __name__ == "__main__":
         make_L22(a.jobs, tuple(a.h) if a.h else ("1.5", "0.5", "3"))
     elif a.target == "L20grad":
         make_L20grad(a.jobs)
+    elif a.target == "L32":
+        make_L32()
     else:
         make_L30(a.jobs)

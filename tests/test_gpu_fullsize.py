@@ -1,4 +1,5 @@
-"""Full-size parity: the five workloads at their configured sizes against stored oracle values.
+"""Full-size parity: the five workloads at their configured sizes, and the largest split-table
+sector (L = 32), against stored oracle values.
 
 The oracle needs minutes to hours per evolution at these sizes, so its values are computed
 once on the host by tests/golden/make_golden.py (which calls only oracle/ and the seeded
@@ -117,4 +118,25 @@ def test_L30_early_times_vs_moment_series(kry, name):
         torch.cuda.empty_cache()
         err = float(np.max(np.abs(P - Po)))
         _report(f"{name} {dtype}, t <= {times[-1]:.3f}", err)
+        assert err <= BAR[dtype]
+
+
+def test_L32_largest_split_sector_vs_moment_series(kry):
+    """The largest sector of the split rank tables: L = 32, N_up = 16 (D = 601,080,390; the
+    lower-bit rank table has 2^16 entries and is read through L1), the quasiperiodic field,
+    against the moment series at the output times its rigorous bound (<= 1e-12) covers, in
+    every precision with a Krylov dimension of 12 (13 vectors of 9.6 GB in complex128)."""
+    L, N = 32, 16
+    times, Po = _golden_P("P_L32_qp_early.txt", "t P bound")[0]
+    assert len(times) >= 3
+    h = workloads.quasiperiodic_field(L, 1.5, workloads.phases(5)[0])
+    B = kry.Basis(L, N)
+    assert B.dim == 601080390
+    for dtype in ("c64", "c128e", "c128"):
+        H = kry.Hamiltonian(B, 1.0, 1.0, h, pbc=True)
+        P, st = H.return_probability(workloads.neel_state(L), list(times), m=12, tol=TOL[dtype], dtype=dtype)
+        H.close()
+        torch.cuda.empty_cache()
+        err = float(np.max(np.abs(P - Po)))
+        _report(f"L32 {dtype}, t <= {times[-1]:.3f} ({st['n_krylov_steps']} Krylov steps)", err)
         assert err <= BAR[dtype]
