@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-l30", action="store_true", help="skip the L = 30 complex64 line")
     ap.add_argument("--l30", action="store_true",
                     help="only the L = 30 configuration in full: both fields, complex128 and complex64, e2e")
+    ap.add_argument("--l32", action="store_true",
+                    help="only the L = 32 sector (D = 601,080,390), complex64, to t = 100")
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the temporal autocorrelation, random-state ensemble and L = 55 ring lines")
     ap.add_argument("--form", default="c128", choices=["c128", "c64", "c64b"],
@@ -511,7 +513,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def l30_leg(kry, workloads, world, tune, clocks, full=False):
+def l32_config(workloads):
+    """The largest sector of the split rank tables: L = 32, N_up = 16 (D = 601,080,390), the
+    quasiperiodic field of the L = 30 workload's seed (h = 1.5), Neel state, m = 30, the 40
+    log times."""
+    c = dict(workloads.config("L30_qp"))
+    c.update(name="L32_qp", L=32, n_up=16, state=workloads.neel_state(32),
+             h=[workloads.quasiperiodic_field(32, 1.5, workloads.phases(5)[0])])
+    return c
+
+
+def l30_leg(kry, workloads, world, tune, clocks, full=False, l32=False):
     """The largest single-GPU configuration: L = 30, N_up = 15 (D = 155,117,520), Neel state,
     m = 30, 40 log times to t = 100.  Default: the quasiperiodic field (h = 1.5) in complex64
     (42 GB of Krylov workspace), one evolution after a short capture run.  full: both fields,
@@ -528,9 +540,13 @@ def l30_leg(kry, workloads, world, tune, clocks, full=False):
     Ps = {}
     cases = ([("L30_qp", "c64")] if not full else
              [(n, d) for n in ("L30_clean", "L30_qp") for d in ("c64", "c128", "c128e")])
+    if l32:   # complex64 only: 31 vectors of 4.8 GB (complex128 would need 298 GB)
+        cases = [("L32_qp", "c64")]
+        res["workload"] = ("L=32 N_up=16 D=601080390 PBC J=1 Delta=1 h=1.5 (phi: phases(5)), Neel psi0, m=30, "
+                           "40 log times in [0.1,100]")
     B = None
     for name, dt in cases:
-        c = workloads.config(name)
+        c = l32_config(workloads) if name == "L32_qp" else workloads.config(name)
         if B is None:
             B = kry.Basis(c["L"], c["n_up"])
         D = B.dim
@@ -792,7 +808,8 @@ def run_ncu_case(args):
 
 
 def run_l30(args):
-    """python bench.py --l30: the L = 30 configuration in full (one JSON line)."""
+    """python bench.py --l30: the L = 30 configuration in full (one JSON line); --l32: the
+    L = 32 sector in complex64."""
     import torch
 
     import paper_1704_02770_gb300 as kry
@@ -809,18 +826,18 @@ def run_l30(args):
     tune = {f"{dt}_K1": H24.autotune(c["state"], 1.0, dtype=dt) for dt in ("c128", "c64")}
     H24.close()
     clk = ClockSampler(local).start()
-    res = l30_leg(kry, workloads, world, tune, {"sm_mhz": None}, full=True)
+    res = l30_leg(kry, workloads, world, tune, {"sm_mhz": None}, full=True, l32=args.l32)
     clocks = clk.stop()
     res.pop("_launches")
     if rank == 0:
-        print(json.dumps({"metric": METRIC, "l30": res, "clocks": clocks,
+        print(json.dumps({"metric": METRIC, ("l32" if args.l32 else "l30"): res, "clocks": clocks,
                           "shapes": {k: v["shape"] for k, v in tune.items()},
                           "measured_peaks": {"fp64_tflops": f64, "fp32_tflops": f32}}))
 
 
 if __name__ == "__main__":
     a = parse()
-    if a.l30:
+    if a.l30 or a.l32:
         run_l30(a)
     elif a.ncu_case:
         run_ncu_case(a)
