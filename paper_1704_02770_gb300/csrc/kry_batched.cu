@@ -46,9 +46,9 @@ __device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, co
     const uint32_t wrap = hm.pbc ? ((s ^ (s >> (L - 1))) & 1u) : 0u;
     const int nanti = __popc(anti) + (int)wrap;
     const R dz = (R)hm.cz * (R)(hm.nbonds - 2 * nanti);
-    V acc[KQ];
+    typename Arith<V>::HvSum acc[KQ];
 #pragma unroll
-    for (int q = 0; q < KQ; ++q) acc[q] = VT<V>::zero();
+    for (int q = 0; q < KQ; ++q) acc[q] = typename Arith<V>::HvSum{};
     // Neighbour rows in chunks of 4 bond positions (bit 31 = ring bond): the ranks are the
     // same for all lanes; every lane issues its loads of the whole chunk before summing.
     const uint32_t hops = anti | (wrap << 31);
@@ -78,14 +78,14 @@ __device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, co
 #pragma unroll
                 for (int q = 0; q < KQ; ++q) {
                     const int k = lane + 32 * q;
-                    if (k < K) v[u][q] = __ldg(xr + k);
+                    if (k < K) v[u][q] = ldg(xr + k);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int q = 0; q < KQ; ++q) acc[q] = acc[q] + v[u][q];
+            for (int q = 0; q < KQ; ++q) hv_add(acc[q], v[u][q]);
     }
     const V *xr = x + (size_t)(base + off) * K;
 #pragma unroll
@@ -93,7 +93,7 @@ __device__ __forceinline__ void hv_row_b(const DevBasis &b, const DevHam &hm, co
         const int k = lane + 32 * q;
         if (k < K) {
             const R d = dz + VT<V>::ehlo(hm, pos * K + k) + VT<V>::ehhi(hm, hi * K + k);
-            out[q] = axpby(d, __ldg(xr + k), (R)hm.halfJ, acc[q]);
+            out[q] = hv_finish(d, ldg(xr + k), (R)hm.halfJ, acc[q]);
         } else {
             out[q] = VT<V>::zero();
         }
@@ -250,11 +250,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
                 for (int rr = 0; rr < RH; ++rr) uu[rr] = VT<V>::zero();
                 if (nr == RH) {
 #pragma unroll
-                    for (int rr = 0; rr < RH; ++rr) uu[rr] = __ldg(a.U + (size_t)(rh + rr) * K + k);
+                    for (int rr = 0; rr < RH; ++rr) uu[rr] = ldg(a.U + (size_t)(rh + rr) * K + k);
                 } else {
 #pragma unroll
                     for (int rr = 0; rr < RH; ++rr)
-                        if (rr < nr) uu[rr] = __ldg(a.U + (size_t)(rh + rr) * K + k);
+                        if (rr < nr) uu[rr] = ldg(a.U + (size_t)(rh + rr) * K + k);
                 }
                 if (g == 0) {
 #pragma unroll
@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_dots_b(EvArgsB<V> a, int jj)
                     const V *wi = a.W + (size_t)iv * a.ldW + (size_t)rh * K + k;
                     if (nr == RH) {
 #pragma unroll
-                        for (int rr = 0; rr < RH; ++rr) dst[rr] = __ldg(wi + (size_t)rr * K);
+                        for (int rr = 0; rr < RH; ++rr) dst[rr] = ldg(wi + (size_t)rr * K);
                     } else {
 #pragma unroll
-                        for (int rr = 0; rr < RH; ++rr) dst[rr] = (rr < nr) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+                        for (int rr = 0; rr < RH; ++rr) dst[rr] = (rr < nr) ? ldg(wi + (size_t)rr * K) : VT<V>::zero();
                     }
                 };
                 // (a prefetch of the next vector's rows, as in the single-realisation dots,
@@ -317,15 +317,17 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
     constexpr int Kp = 32 * KQ, NG = NTHR / Kp, QD = (MMAX + NG) / NG;
     const int nvec = (MODE == 2) ? ctl->hd.m_run : ((MODE == 3 || MODE == 4) ? 0 : jj + 1);
     extern __shared__ __align__(16) unsigned char smem[];
-    V *coef = (V *)smem;                          // [MMAX+1][Kp]
-    V *wtile = coef + (MMAX + 1) * Kp;            // [TROWS][Kp]
+    using Coef = typename Arith<V>::Coef;
+    static_assert(sizeof(Coef) == sizeof(V), "coefficient slots have the element size");
+    Coef *coef = (Coef *)smem;                    // [MMAX+1][Kp]
+    V *wtile = (V *)(coef + (MMAX + 1) * Kp);     // [TROWS][Kp]
     double2 *nred = (double2 *)(wtile + TROWS * Kp);   // [NG][Kp] (norm), then [NG][Kp] (G)
     const int tid = threadIdx.x, K = a.K;
     for (int e = tid; e < nvec * Kp; e += NTHR) {
         const int i = e / Kp, k = e % Kp;
         double2 c = make_double2(0.0, 0.0);
         if (k < K) c = (MODE == 0) ? ctl->coefA[i][k] : (MODE == 1) ? ctl->coefC[i][k] : ctl->coefY[i][k];
-        coef[i * Kp + k] = VT<V>::from(c);
+        coef[i * Kp + k] = coef_from<V>(c);
     }
     __syncthreads();
     V *out = (MODE == 2 || MODE == 3) ? a.W : a.W + (size_t)(jj + 1) * a.ldW;
@@ -342,17 +344,18 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
                 const size_t idx = (size_t)(r0 + rr) * K + k;
                 if (src) w = src[idx];
                 if (MODE != 4) {
+                    typename Arith<V>::Lin wl = lin_init(w);
                     if (MODE == 2) {
 #pragma unroll 8
-                        for (int i = 0; i < nvec; ++i) w = cfms(coef[i * Kp + k], a.W[(size_t)i * a.ldW + idx], w);
+                        for (int i = 0; i < nvec; ++i) lin_fms(wl, coef[i * Kp + k], a.W[(size_t)i * a.ldW + idx]);
                     } else {
 #pragma unroll 8
-                        for (int i = 0; i < nvec; ++i)
-                            w = cfms(coef[i * Kp + k], __ldg(a.W + (size_t)i * a.ldW + idx), w);
+                        for (int i = 0; i < nvec; ++i) lin_fms(wl, coef[i * Kp + k], ldg(a.W + (size_t)i * a.ldW + idx));
                     }
+                    w = (MODE == 3) ? w : lin_out(wl);
                     out[idx] = w;
-                    nrm.add(w, w);
-                    if (a.G && MODE != 3) gacc.add(__ldg(a.G + idx), w);
+                    nrm.add_norm(w);
+                    if (a.G && MODE != 3) gacc.add(ldg(a.G + idx), w);
                 }
             }
             if (MODE == 4) wtile[rr * Kp + k] = w;
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_lincomb_b(EvArgsB<V> a, int jj)
                         V vv[TROWS];
 #pragma unroll
                         for (int rr = 0; rr < TROWS; ++rr)
-                            vv[rr] = (r0 + rr < D) ? __ldg(wi + (size_t)rr * K) : VT<V>::zero();
+                            vv[rr] = (r0 + rr < D) ? ldg(wi + (size_t)rr * K) : VT<V>::zero();
 #pragma unroll
                         for (int rr = 0; rr < TROWS; ++rr) acc[q].add(vv[rr], wtile[rr * Kp + k]);
                         acc[q].renorm();
@@ -577,11 +580,7 @@ template <class V>
 __global__ void k_set_basis_state_b(V *W0, int K, const KryCtlB *ctl)
 {
     const int k = threadIdx.x;
-    if (k < K) {
-        V one = VT<V>::zero();
-        one.x = 1;
-        W0[(size_t)ctl->r0k[k] * K + k] = one;
-    }
+    if (k < K) W0[(size_t)ctl->r0k[k] * K + k] = VT<V>::from(make_double2(1.0, 0.0));
 }
 
 // ---------------------------------------------------------------- launchers
@@ -655,7 +654,12 @@ int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s, int pa
         return KRY_OK;
     }
     if (a.b.list) {
-        if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
+        if constexpr (std::is_same<V, ffc>::value) {
+            set_error("batched float-float vectors need the split-table basis");
+            return KRY_EINVAL;
+        } else {
+            if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
+        }
         if (part == 1) return KRY_OK;
         KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
         KRY_CU(cudaGetLastError());
@@ -745,14 +749,18 @@ int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const voi
     return KRY_OK;
 }
 
-int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s)
+int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s, int ff)
 {
     if (c64) k_set_basis_state_b<float2><<<1, KBMAX, 0, s>>>((float2 *)W0, K, ctl);
+    else if (ff) k_set_basis_state_b<ffc><<<1, KBMAX, 0, s>>>((ffc *)W0, K, ctl);
     else k_set_basis_state_b<double2><<<1, KBMAX, 0, s>>>((double2 *)W0, K, ctl);
     KRY_CU(cudaGetLastError());
     return KRY_OK;
 }
 
+template int batched_grid<ffc>(const DevBasis &, int, int, int *);
+template int launch_passA_b<ffc>(const EvArgsB<ffc> &, int, int, cudaStream_t, int);
+template int launch_lincomb_b<ffc>(const EvArgsB<ffc> &, int, int, int, cudaStream_t);
 template int batched_grid<double2>(const DevBasis &, int, int, int *);
 template int batched_grid<float2>(const DevBasis &, int, int, int *);
 template int launch_passA_b<double2>(const EvArgsB<double2> &, int, int, cudaStream_t, int);

@@ -205,6 +205,17 @@ __device__ __forceinline__ void lin_fms(FF4 &w, float4 c, ffc x)
 template <class V> __device__ __forceinline__ V pre(V u) { return u; }
 
 __device__ __forceinline__ double2 scale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// s a for a float-float element: the product of the split scale with each component
+__device__ __forceinline__ ffc scale(ffc a, double s)
+{
+    const float2 f = dsplit(s);
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    ff_mac(f.x, f.y, a.xh, a.xl, sr, cr);
+    ff_mac(f.x, f.y, a.yh, a.yl, si, ci);
+    ff_renorm(sr, cr);
+    ff_renorm(si, ci);
+    return ffc{sr, cr, si, ci};
+}
 __device__ __forceinline__ float2 scale(float2 a, double s) { return make_float2(a.x * (float)s, a.y * (float)s); }
 __device__ __forceinline__ float2 scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 

@@ -505,8 +505,9 @@ int grid_for_b(const kry_ham_s *H, int dtype, int *gridB)
 {
     const DevBasis &b = H->b->dev;
     const int Kp = padded_k(H->K);
-    const int g = dtype == KRY_C64 ? batched_grid<float2>(b, Kp, rl_in_smem(b), gridB)
-                                   : batched_grid<double2>(b, Kp, rl_in_smem(b), gridB);
+    const int g = dtype == KRY_C64     ? batched_grid<float2>(b, Kp, rl_in_smem(b), gridB)
+                  : dtype == KRY_C128E ? batched_grid<ffc>(b, Kp, rl_in_smem(b), gridB)
+                                       : batched_grid<double2>(b, Kp, rl_in_smem(b), gridB);
     const int ov = H->shape[dtype_slot(dtype)][0];
     if (g > 0 && ov > 0) *gridB = ov;
     return g;
@@ -600,6 +601,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     ea.W = a.W;
     ea.ldW = l.ldW;
     ea.c64 = dtype == KRY_C64;
+    ea.ff = std::is_same<V, ffc>::value;
     ea.K = K;
     const int want_C = C_out ? 1 : 0;
     if (want_C) {
@@ -634,7 +636,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     hd.t_end = times[n_times - 1];
     hd.tol = tol;
     hd.n_times = n_times;
-    hd.eta_corr = dtype == KRY_C64 ? 1e-5 : 1e-12;
+    hd.eta_corr = dtype == KRY_C64 ? 1e-5 : dtype == KRY_C128E ? 3e-11 : 1e-12;
     hd.eta_cancel = 0.1;
     hd.verify = H->orth_check;
     hd.eta_bd = dtype == KRY_C64 ? 1e-6 : 1e-12;
@@ -667,13 +669,18 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     delete c;
     if (ce != cudaSuccess) return cuda_fail(ce, "control block upload");
     KRY_CU(cudaMemcpyAsync((void *)ea.times, times, sizeof(double) * n_times, cudaMemcpyHostToDevice, s));
+    constexpr bool FF = std::is_same<V, ffc>::value;   // complex128 in and out, float-float inside
     if (general) {
-        KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        if (FF) {
+            if (int rc = launch_c128_to_ffc(d_psi0, (void *)a.G, nvec, s)) return rc;
+        } else {
+            KRY_CU(cudaMemcpyAsync((void *)a.G, d_psi0, nvec * es, cudaMemcpyDeviceToDevice, s));
+        }
         if (int rc = launch_lincomb_b<V>(a, 3, 0, gridB, s)) return rc;
         if (int rc = launch_reduce_b(a.ctl, a.part, gridB, K, Kp, 5, 0, 1, 0, s)) return rc;
     } else {
         KRY_CU(cudaMemsetAsync(a.W, 0, nvec * es, s));
-        if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, a.ctl, s)) return rc;
+        if (int rc = launch_set_basis_state_b(a.W, dtype == KRY_C64, K, a.ctl, s, FF)) return rc;
     }
     KryHdrB *hp = (KryHdrB *)H->h_poll;
     long long launched = 0;
@@ -713,7 +720,11 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
     }
     KRY_CU(cudaMemcpyAsync(P_out, ea.P, sizeof(double) * n_times * K, cudaMemcpyDeviceToHost, s));
     if (want_C) KRY_CU(cudaMemcpyAsync(C_out, ea.C, sizeof(double) * n_times * K, cudaMemcpyDeviceToHost, s));
-    if (d_psi_out) KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    if (d_psi_out && FF) {
+        if (int rc = launch_ffc_to_c128(a.W, d_psi_out, nvec, s)) return rc;
+    } else if (d_psi_out) {
+        KRY_CU(cudaMemcpyAsync(d_psi_out, a.W, nvec * es, cudaMemcpyDeviceToDevice, s));
+    }
     std::vector<double> orth(K);
     KRY_CU(cudaMemcpyAsync(orth.data(), a.ctl->orth, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
     KRY_CU(cudaStreamSynchronize(s));
@@ -741,8 +752,8 @@ int check_evolve_args(kry_ham H, int dtype, const double *times, int n_times, in
         set_error("kry_evolve: bad arguments (need H, times, n_times >= 1, P_out, 1 <= m <= %d, tol > 0)", MMAX);
         return KRY_EINVAL;
     }
-    if (dtype == KRY_C128E && (H->K > 1 || H->b->dev.list)) {
-        set_error("kry_evolve: KRY_C128E serves single-realisation evolutions on split-table bases (L <= 32)");
+    if (dtype == KRY_C128E && H->b->dev.list) {
+        set_error("kry_evolve: KRY_C128E serves split-table bases (L <= 32)");
         return KRY_EINVAL;
     }
     for (int i = 0; i < n_times; ++i) {
@@ -796,7 +807,7 @@ extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *l
 extern "C" int64_t kry_workspace_bytes(kry_ham H, int dtype, int m, int n_times)
 {
     if (!H || m < 1 || m > MMAX || n_times < 1 || !dtype_ok(dtype)) return -1;
-    if (dtype == KRY_C128E && (H->K > 1 || H->b->dev.list)) return -1;
+    if (dtype == KRY_C128E && H->b->dev.list) return -1;
     if (H->K > 1) {
         int gridB = 0;
         const int grid = grid_for_b(H, dtype, &gridB);
@@ -848,7 +859,9 @@ extern "C" int kry_evolve(kry_ham H, int dtype, const void *d_psi0, const double
     if (!d_psi0) { set_error("kry_evolve: d_psi0 is NULL"); return KRY_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C128E)
-        return evolve_t<ffc>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
+        return H->K > 1
+                   ? evolve_bt<ffc>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
+                   : evolve_t<ffc>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, d_psi0, 0, true, times, n_times, m, tol, d_psi_out, P_out, stats, s)
@@ -870,7 +883,9 @@ extern "C" int kry_return_probability(kry_ham H, int dtype, uint64_t psi0_state,
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == KRY_C128E)
-        return evolve_t<ffc>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
+        return H->K > 1
+                   ? evolve_bt<ffc>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
+                   : evolve_t<ffc>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s);
     if (dtype == KRY_C64)
         return H->K > 1
                    ? evolve_bt<float2>(H, dtype, nullptr, psi0_state, false, times, n_times, m, tol, nullptr, P_out, stats, s)
@@ -904,6 +919,9 @@ int evolve_states(kry_ham H, int dtype, const uint64_t *states, const double *ti
         return dtype == KRY_C64
                    ? evolve_bt<float2>(H, dtype, nullptr, 0, false, times, n_times, m, tol, nullptr, P_out, stats, s,
                                        states, C_out)
+               : dtype == KRY_C128E
+                   ? evolve_bt<ffc>(H, dtype, nullptr, 0, false, times, n_times, m, tol, nullptr, P_out, stats, s,
+                                    states, C_out)
                    : evolve_bt<double2>(H, dtype, nullptr, 0, false, times, n_times, m, tol, nullptr, P_out, stats, s,
                                         states, C_out);
     EvOpts opt;

@@ -417,6 +417,7 @@ __device__ void load_tridiag_b(ExpSmem &sm, const KryCtlB *ctl, int k, int me, c
             const size_t idx = (size_t)lane * ea.ldW + (size_t)ctl->r0k[k] * ea.K + k;
             double2 w;
             if (ea.c64) { float2 f = ((const float2 *)ea.W)[idx]; w = make_double2(f.x, f.y); }
+            else if (ea.ff) { float4 f = ((const float4 *)ea.W)[idx]; w = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w); }
             else w = ((const double2 *)ea.W)[idx];
             const double s = ctl->sigma[lane][k];
             g = make_double2(w.x * s, w.y * s);

@@ -174,6 +174,7 @@ struct ExpArgsB {
     const void *W;
     size_t ldW;
     int c64, K;
+    int ff;          // the vectors are float-float (ffc)
     double *C;       // nullable: temporal autocorrelation [n_times][K]
     const double *glx, *glw;   // Gauss-Legendre nodes and weights on [-1, 1] (with C)
 };
@@ -186,7 +187,7 @@ int launch_reduce_b(KryCtlB *ctl, const double2 *part, int grid, int K, int Kp, 
 template <class V> int batched_grid(const DevBasis &b, int Kp, int rl_smem, int *gridB);
 int launch_apply_b(const DevBasis &b, const DevHam &h, int c64, int K, const void *x, void *y,
                    int rl_smem, cudaStream_t s);
-int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s);
+int launch_set_basis_state_b(void *W0, int c64, int K, const KryCtlB *ctl, cudaStream_t s, int ff = 0);
 int launch_exp_b(const ExpArgsB &a, cudaStream_t s);
 
 // Device control block of one evolution: Lanczos coefficients of the current Krylov

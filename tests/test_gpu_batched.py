@@ -48,7 +48,7 @@ def test_identical_copies_equal_single_run(kry):
         assert np.max(np.abs(PK[:, k] - P1)) <= 1e-12
 
 
-@pytest.mark.parametrize("dtype,bar", [("c128", 1e-10), ("c64", 1e-5)])
+@pytest.mark.parametrize("dtype,bar", [("c128", 1e-10), ("c64", 1e-5), ("c128e", 1e-10)])
 def test_each_realisation_matches_oracle(kry, dtype, bar):
     L, N, K = 14, 7, 6
     h = _fields(L, 1.5, 3, K)
@@ -56,7 +56,7 @@ def test_each_realisation_matches_oracle(kry, dtype, bar):
     st = workloads.neel_state(L)
     B = kry.Basis(L, N)
     P, _ = kry.Hamiltonian(B, 1.0, 1.0, h).return_probability(
-        st, times, tol=1e-10 if dtype == "c128" else 1e-7, dtype=dtype)
+        st, times, tol=1e-7 if dtype == "c64" else 1e-10, dtype=dtype)
     worst = 0.0
     for k in range(K):
         Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
@@ -66,7 +66,7 @@ def test_each_realisation_matches_oracle(kry, dtype, bar):
     assert worst <= bar
 
 
-@pytest.mark.parametrize("dtype,bound", [("c128", 1e-12), ("c64", 2e-5)])
+@pytest.mark.parametrize("dtype,bound", [("c128", 1e-12), ("c64", 2e-5), ("c128e", 1e-12)])
 def test_orthogonality_check_batched(kry, dtype, bound):
     """Every realisation of a batch keeps each new Lanczos vector orthogonal to the previous
     ones after one classical Gram-Schmidt pass: measured after every update with orth_check
@@ -77,17 +77,20 @@ def test_orthogonality_check_batched(kry, dtype, bound):
     times = workloads.log_times(12, 0.1, 30.0)
     st = workloads.neel_state(L)
     H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, h)
-    tol = 1e-10 if dtype == "c128" else 1e-7
+    tol = 1e-7 if dtype == "c64" else 1e-10
     P0, _ = H.return_probability(st, times, tol=tol, dtype=dtype)
     H.orth_check(True)
     P1, st1 = H.return_probability(st, times, tol=tol, dtype=dtype)
     H.orth_check(False)
     print(f"[orth] batched L14 K=6 {dtype}: max |<v_i, w>|/||w|| = {st1['max_orth_loss']:.2e}")
     assert 0.0 < st1["max_orth_loss"] <= bound
-    assert np.max(np.abs(P1 - P0)) <= (1e-12 if dtype == "c128" else 1e-6)
+    assert np.max(np.abs(P1 - P0)) <= (1e-6 if dtype == "c64" else 1e-12)
 
 
-def test_general_initial_states_batched(kry):
+@pytest.mark.parametrize("emulated", [False, True])
+def test_general_initial_states_batched(kry, emulated):
+    """Dense complex128 initial vectors [D][K] and psi(t) out, in FP64 and with float-float
+    vectors inside (complex128 in and out)."""
     L, N, K = 10, 5, 4
     h = _fields(L, 1.0, 9, K)
     B = kry.Basis(L, N)
@@ -98,10 +101,31 @@ def test_general_initial_states_batched(kry):
     times = [0.0, 0.4, 3.0]
     x = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
     out = torch.empty_like(x)
-    P, _ = H.evolve(x, times, tol=1e-10, psi_out=out)
+    P, _ = H.evolve(x, times, tol=1e-10, psi_out=out, emulated=emulated)
     out = out.cpu().numpy()
     for k in range(K):
         Hc = ob.CSR(L, N, 1.0, 1.0, h[k], True)
         Po, psio, _ = krylov.evolve(Hc.matvec, Hc.norm_inf(), psi0[:, k].copy(), times, m=30, tol=1e-12)
         assert np.max(np.abs(P[:, k] - Po)) <= 1e-10
         assert np.linalg.norm(out[:, k] - psio) <= 1e-10
+
+
+def test_float_float_batch_against_fp64_batch(kry):
+    """The K = 16 phase ensemble of L = 16 in float-float against the FP64 batch: the same
+    recurrences to rounding (about 1e-14), and a batch of identical copies reproduces the
+    single float-float run."""
+    L, N, K = 16, 8, 16
+    h = _fields(L, 1.5, 3, K)
+    times = workloads.log_times(20, 0.1, 30.0)
+    st = workloads.neel_state(L)
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, h)
+    Pe, ste = H.return_probability(st, times, dtype="c128e")
+    P8, st8 = H.return_probability(st, times, dtype="c128")
+    d = float(np.max(np.abs(Pe - P8)))
+    print(f"[parity] batched L16 K=16 c128e vs c128: max|dP| = {d:.3e}")
+    assert d <= 1e-12 and ste["n_second_pass"] == 0
+    H1 = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, h[0])
+    P1, _ = H1.return_probability(st, times, dtype="c128e")
+    Hc = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, np.tile(h[0], (3, 1)))
+    Pc, _ = Hc.return_probability(st, times, dtype="c128e")
+    assert np.max(np.abs(Pc - P1[:, None])) <= 1e-12
