@@ -57,9 +57,9 @@ enum { KRY_OBC = 0, KRY_PBC = 1 };
  * held as float-float pairs (16 bytes per element, about 48 significant bits) and the vector
  * arithmetic (H.v sums, dots, updates) done in float-float on the FP32 pipe, because GB300
  * runs FP64 at 1/64 of its FP32 rate; the Lanczos coefficients, the small exponential and the
- * step control stay FP64.  KRY_C128E serves the split-table bases (L <= 32), single
- * realisations and batched ones (K > 1, [D][K] as for the other dtypes); on the sorted-list
- * basis it returns KRY_EINVAL. */
+ * step control stay FP64.  KRY_C128E serves every basis and both single and batched
+ * (K > 1, [D][K]) evolutions, like the other dtypes; kry_apply and kry_grad take KRY_C128 and
+ * KRY_C64 only. */
 enum { KRY_C128 = 0, KRY_C64 = 1, KRY_C128E = 2 };
 
 /* Counters of one kry_evolve / kry_return_probability call. */

@@ -654,12 +654,7 @@ int launch_passA_b(const EvArgsB<V> &a, int jj, int grid, cudaStream_t s, int pa
         return KRY_OK;
     }
     if (a.b.list) {
-        if constexpr (std::is_same<V, ffc>::value) {
-            set_error("batched float-float vectors need the split-table basis");
-            return KRY_EINVAL;
-        } else {
-            if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
-        }
+        if (int rc = launch_list_hv_b<V>(a, jj, s)) return rc;
         if (part == 1) return KRY_OK;
         KRY_KQ_SWITCH(a.Kp, { k_dots_b<V, KQ><<<grid, NTHR, 0, s>>>(a, jj); });
         KRY_CU(cudaGetLastError());

@@ -752,10 +752,6 @@ int check_evolve_args(kry_ham H, int dtype, const double *times, int n_times, in
         set_error("kry_evolve: bad arguments (need H, times, n_times >= 1, P_out, 1 <= m <= %d, tol > 0)", MMAX);
         return KRY_EINVAL;
     }
-    if (dtype == KRY_C128E && H->b->dev.list) {
-        set_error("kry_evolve: KRY_C128E serves split-table bases (L <= 32)");
-        return KRY_EINVAL;
-    }
     for (int i = 0; i < n_times; ++i) {
         if (!(times[i] >= 0.0) || !std::isfinite(times[i]) || (i > 0 && times[i] < times[i - 1])) {
             set_error("kry_evolve: times must be finite, non-negative and non-decreasing");
@@ -807,7 +803,6 @@ extern "C" int kry_profile_read(kry_ham H, double *ms, double *bytes, int64_t *l
 extern "C" int64_t kry_workspace_bytes(kry_ham H, int dtype, int m, int n_times)
 {
     if (!H || m < 1 || m > MMAX || n_times < 1 || !dtype_ok(dtype)) return -1;
-    if (dtype == KRY_C128E && H->b->dev.list) return -1;
     if (H->K > 1) {
         int gridB = 0;
         const int grid = grid_for_b(H, dtype, &gridB);

@@ -725,10 +725,8 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
         return (int)std::max<uint32_t>(1u, std::min<uint32_t>(ntiles, (uint32_t)(sm_count() * std::max(1, occ))));
     };
     *gridH = fit(occH);
-    if constexpr (!std::is_same<V, ffc>::value) {
-        if (b.list) {
-            if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
-        }
+    if (b.list) {
+        if (int rc = list_hv_grid<V>(b, gridH)) return -rc;
     }
     *gridB = fit(occB);
     return fit(occA);
@@ -737,9 +735,7 @@ int vector_grid(const DevBasis &b, int rl_smem, int hv_form, int *gridH, int *gr
 template <class V>
 int launch_hv(const EvArgs<V> &a, int jj, int grid, cudaStream_t s, int pdl)
 {
-    if constexpr (!std::is_same<V, ffc>::value) {
-        if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
-    }
+    if (a.b.list) return launch_list_hv<V>(a, jj, grid, s, pdl);
     EvArgs<V> ah = a;
     ah.rl_smem = a.rl_smem && !(a.hv_form & 2);
     const size_t smem = apply_smem(a.b, ah.rl_smem, sizeof(V) == sizeof(float2));

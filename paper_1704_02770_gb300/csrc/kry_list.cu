@@ -61,8 +61,10 @@ __device__ __forceinline__ uint32_t list_rank(uint64_t s, const uint32_t *cb, in
 // Row r (state s) of H x for realisation k of K interleaved ones: returns the sum of the
 // neighbour amplitudes, and the diagonal d(s) in *d.
 template <class V>
-__device__ __forceinline__ V list_row(const DevBasis &b, const DevHam &hm, const V *__restrict__ x, uint32_t r,
-                                      uint64_t s, int k, int K, const uint32_t *cb, typename VT<V>::R *d)
+__device__ __forceinline__ typename Arith<V>::HvSum list_row(const DevBasis &b, const DevHam &hm,
+                                                             const V *__restrict__ x, uint32_t r, uint64_t s,
+                                                             int k, int K, const uint32_t *cb,
+                                                             typename VT<V>::R *d)
 {
     using R = typename VT<V>::R;
     const int L = b.L, N1 = b.N + 1;
@@ -76,7 +78,7 @@ __device__ __forceinline__ V list_row(const DevBasis &b, const DevHam &hm, const
         e += VT<V>::eh8(hm, ((size_t)c * 256 + v) * K + k);
     }
     *d = e;
-    V acc = VT<V>::zero();
+    typename Arith<V>::HvSum acc{};
     uint64_t a = anti;
     while (a) {
         const int p = __ffsll((long long)a) - 1;
@@ -84,11 +86,11 @@ __device__ __forceinline__ V list_row(const DevBasis &b, const DevHam &hm, const
         const int cnt = __popcll((long long)(s & ((1ull << p) - 1ull)));
         const uint32_t step = cb[p * N1 + cnt];
         const uint32_t t = ((s >> p) & 1ull) ? r + step : r - step;
-        acc = acc + __ldg(x + (size_t)t * K + k);
+        hv_add(acc, ldg(x + (size_t)t * K + k));
     }
     if (wrap) {
         const uint64_t s2 = s ^ ((1ull << (L - 1)) | 1ull);
-        acc = acc + __ldg(x + (size_t)list_rank(s2, cb, N1) * K + k);
+        hv_add(acc, ldg(x + (size_t)list_rank(s2, cb, N1) * K + k));
     }
     return acc;
 }
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(NTHR) k_list_apply(DevBasis b, DevHam hm, int 
         const uint32_t r = (uint32_t)(i / (size_t)K);
         const int k = (int)(i - (size_t)r * K);
         R d;
-        const V acc = list_row<V>(b, hm, x, r, __ldg(b.states + r), k, K, cb, &d);
-        y[i] = axpby(d, __ldg(x + i), (R)hm.halfJ, acc);
+        const auto acc = list_row<V>(b, hm, x, r, __ldg(b.states + r), k, K, cb, &d);
+        y[i] = hv_finish(d, ldg(x + i), (R)hm.halfJ, acc);
     }
 }
 
@@ -181,8 +183,8 @@ __global__ void __launch_bounds__(NTHR) k_list_hv(EvArgs<V> a, int jj)
     const V *x = a.W + (size_t)jj * a.ldW;
     for (uint32_t r = blockIdx.x * NTHR + threadIdx.x; r < a.b.D; r += gridDim.x * NTHR) {
         R d;
-        const V acc = list_row<V>(a.b, a.h, x, r, __ldg(a.b.states + r), 0, 1, cb, &d);
-        a.U[r] = axpby(sj * d, __ldg(x + r), shj, acc);
+        const auto acc = list_row<V>(a.b, a.h, x, r, __ldg(a.b.states + r), 0, 1, cb, &d);
+        a.U[r] = hv_finish(sj * d, ldg(x + r), shj, acc);
     }
 }
 
@@ -204,9 +206,9 @@ __global__ void __launch_bounds__(NTHR) k_list_hv_b(EvArgsB<V> a, int jj)
         const uint32_t r = (uint32_t)(i / (size_t)K);
         const int k = (int)(i - (size_t)r * K);
         R d;
-        const V acc = list_row<V>(a.b, a.h, x, r, __ldg(a.b.states + r), k, K, cb, &d);
+        const auto acc = list_row<V>(a.b, a.h, x, r, __ldg(a.b.states + r), k, K, cb, &d);
         const double sd = ctl->sigma[jj][k];
-        a.U[i] = axpby((R)sd * d, __ldg(x + i), (R)(sd * a.h.halfJ), acc);
+        a.U[i] = hv_finish((R)sd * d, ldg(x + i), (R)(sd * a.h.halfJ), acc);
     }
 }
 
@@ -302,6 +304,9 @@ int launch_list_hv_b(const EvArgsB<V> &a, int jj, cudaStream_t s)
     return KRY_OK;
 }
 
+template int list_hv_grid<ffc>(const DevBasis &, int *);
+template int launch_list_hv<ffc>(const EvArgs<ffc> &, int, int, cudaStream_t, int);
+template int launch_list_hv_b<ffc>(const EvArgsB<ffc> &, int, cudaStream_t);
 template int list_hv_grid<double2>(const DevBasis &, int *);
 template int list_hv_grid<float2>(const DevBasis &, int *);
 template int launch_list_hv<double2>(const EvArgs<double2> &, int, int, cudaStream_t, int);

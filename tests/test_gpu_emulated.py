@@ -149,18 +149,23 @@ def test_autocorrelation_matches_fp64(kry):
     assert np.max(np.abs(Ce - C8)) <= 1e-11 and np.max(np.abs(Pe - P8)) <= 1e-11
 
 
-def test_unsupported_uses_are_rejected(kry):
-    """The float-float form serves the split-table bases (single and batched); the sorted-list
-    basis is refused with KRY_EINVAL."""
+def test_batched_and_list_bases(kry):
+    """The float-float form serves batched realisations and the sorted-list basis like the
+    other dtypes (same workspace as complex128): against the FP64 form on a K = 3 batch of
+    L = 10 and on the sorted-list basis of L = 10 and L = 40 (N = 2)."""
     L, N = 10, 5
     hs = [workloads.quasiperiodic_field(L, 1.0, p) for p in workloads.phases(3, 3)]
+    times = workloads.log_times(12, 0.1, 20.0)
     Hb = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs)
-    P, _ = Hb.return_probability(workloads.neel_state(L), [1.0], dtype="c128e")
-    assert P.shape == (1, 3)
+    Pb, _ = Hb.return_probability(workloads.neel_state(L), times, dtype="c128e")
+    Pb8, _ = Hb.return_probability(workloads.neel_state(L), times, dtype="c128")
+    assert Pb.shape == (len(times), 3) and np.max(np.abs(Pb - Pb8)) <= 1e-12
     assert Hb.workspace_size("c128e") == Hb.workspace_size("c128")
-    Hl = kry.Hamiltonian(kry.Basis(L, N, list=True), 1.0, 1.0, hs[0])
-    with pytest.raises(kry.KryError) as e:
-        Hl.return_probability(workloads.neel_state(L), [1.0], dtype="c128e")
-    assert e.value.code == kry.KRY_EINVAL
-    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, hs[0])
-    assert H.workspace_size("c128e") == H.workspace_size("c128")
+    for LL, NN, st in ((L, N, workloads.neel_state(L)), (40, 2, (1 << 0) | (1 << 20))):
+        h = workloads.quasiperiodic_field(LL, 1.0, 0.3)
+        Hl = kry.Hamiltonian(kry.Basis(LL, NN, list=True), 1.0, 1.0, h)
+        Pl, _ = Hl.return_probability(st, times, dtype="c128e")
+        Pl8, _ = Hl.return_probability(st, times, dtype="c128")
+        d = float(np.max(np.abs(Pl - Pl8)))
+        print(f"[parity] list basis L{LL} N{NN} c128e vs c128: max|dP| = {d:.3e}")
+        assert d <= 1e-12

@@ -133,9 +133,9 @@ def test_free_fermions_L55(kry):
     st = (1 << 5) | (1 << 20) | (1 << 40)
     times = workloads.log_times(25, 0.1, 50.0)
     B = kry.Basis(L, N)
-    for dtype, bar in (("c128", 1e-10), ("c64", 1e-5)):
+    for dtype, bar in (("c128", 1e-10), ("c64", 1e-5), ("c128e", 1e-10)):
         P, _ = kry.Hamiltonian(B, 1.0, 0.0, h).return_probability(st, times, dtype=dtype,
-                                                                   tol=1e-10 if dtype == "c128" else 1e-7)
+                                                                   tol=1e-7 if dtype == "c64" else 1e-10)
         Pf = dense.free_fermion_P(L, 1.0, h, True, st, times)
         print(f"[parity] free fermions L55 N3 {dtype}: max|dP| = {np.max(np.abs(P - Pf)):.3e}")
         assert np.max(np.abs(P - Pf)) <= bar
@@ -149,11 +149,12 @@ def test_interacting_L55_vs_oracle_krylov(kry):
     st = (1 << 0) | (1 << 18) | (1 << 36)
     times = workloads.log_times(20, 0.1, 20.0)
     B = kry.Basis(L, N)
-    P, _ = kry.Hamiltonian(B, 1.0, 1.0, h).return_probability(st, times)
     Hc = ob.CSR(L, N, 1.0, 1.0, h, True)
     Po, _ = krylov.return_probability(Hc, ob.lookup(Hc.basis, st), times, m=30, tol=1e-12)
-    print(f"[parity] AA L55 N3: max|dP| = {np.max(np.abs(P - Po)):.3e}")
-    assert np.max(np.abs(P - Po)) <= 1e-10
+    for dtype in ("c128", "c128e"):
+        P, _ = kry.Hamiltonian(B, 1.0, 1.0, h).return_probability(st, times, dtype=dtype)
+        print(f"[parity] AA L55 N3 {dtype}: max|dP| = {np.max(np.abs(P - Po)):.3e}")
+        assert np.max(np.abs(P - Po)) <= 1e-10
 
 
 def test_list_matches_split_tables_P(kry):
