@@ -58,8 +58,8 @@ enum { KRY_OBC = 0, KRY_PBC = 1 };
  * arithmetic (H.v sums, dots, updates) done in float-float on the FP32 pipe, because GB300
  * runs FP64 at 1/64 of its FP32 rate; the Lanczos coefficients, the small exponential and the
  * step control stay FP64.  KRY_C128E serves every basis and both single and batched
- * (K > 1, [D][K]) evolutions, like the other dtypes; kry_apply and kry_grad take KRY_C128 and
- * KRY_C64 only. */
+ * (K > 1, [D][K]) evolutions, like the other dtypes; kry_apply takes KRY_C128 and KRY_C64
+ * only, and kry_grad runs in complex128. */
 enum { KRY_C128 = 0, KRY_C64 = 1, KRY_C128E = 2 };
 
 /* Counters of one kry_evolve / kry_return_probability call. */
