@@ -125,11 +125,19 @@ def _dtype_code(t, emulated: bool = False):
     raise TypeError(f"unsupported dtype {t.dtype}: use complex128 or complex64")
 
 
-def _dev_ptr(t, n=None):
+def _dev_ptr(t, n=None, dtype=None):
+    """The device address of a tensor that the library reads or writes as n elements of
+    `dtype`: anything else (another element type or size, host memory, a strided view, a
+    tensor of another device) is refused here, before a kernel could touch memory outside it."""
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected a {dtype} tensor, got {t.dtype}")
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     if n is not None and t.numel() != n:
         raise ValueError(f"expected {n} elements, got {t.numel()}")
+    import torch
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"tensor on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -153,17 +161,19 @@ class Basis:
         self.dim = int(lib.kry_basis_dim(h))
 
     def rank(self, states, stream=None):
+        """Ranks (int32) of the basis states in an int64 CUDA tensor (kry_basis_rank)."""
         import torch
+        ptr = _dev_ptr(states, dtype=torch.int64)
         out = torch.empty(states.numel(), dtype=torch.int32, device=states.device)
-        _check(load().kry_basis_rank(self._h, _dev_ptr(states), _dev_ptr(out), states.numel(),
-                                     _stream(stream)))
+        _check(load().kry_basis_rank(self._h, ptr, _dev_ptr(out), states.numel(), _stream(stream)))
         return out
 
     def unrank(self, ranks, stream=None):
+        """Basis states (int64) of the ranks in an int32 CUDA tensor (kry_basis_unrank)."""
         import torch
+        ptr = _dev_ptr(ranks, dtype=torch.int32)
         out = torch.empty(ranks.numel(), dtype=torch.int64, device=ranks.device)
-        _check(load().kry_basis_unrank(self._h, _dev_ptr(ranks), _dev_ptr(out), ranks.numel(),
-                                       _stream(stream)))
+        _check(load().kry_basis_unrank(self._h, ptr, _dev_ptr(out), ranks.numel(), _stream(stream)))
         return out
 
     def close(self):
@@ -196,9 +206,11 @@ class Hamiltonian:
 
     def apply(self, x, out=None, stream=None):
         import torch
-        y = torch.empty_like(x) if out is None else out
+        code = _dtype_code(x)
         n = self.basis.dim * self.K
-        _check(load().kry_apply(self._h, _dtype_code(x), _dev_ptr(x, n), _dev_ptr(y, n), _stream(stream)))
+        px = _dev_ptr(x, n)
+        y = torch.empty_like(x) if out is None else out
+        _check(load().kry_apply(self._h, code, px, _dev_ptr(y, n, x.dtype), _stream(stream)))
         return y
 
     def evolve(self, psi0, times, m: int = 30, tol: float = 1e-10, psi_out=None, emulated: bool = False,
@@ -210,8 +222,10 @@ class Hamiltonian:
         P = np.zeros(t.size * self.K)
         st = Stats()
         n = self.basis.dim * self.K
-        _check(load().kry_evolve(self._h, _dtype_code(psi0, emulated), _dev_ptr(psi0, n), tp, t.size, m, tol,
-                                 _dev_ptr(psi_out, n) if psi_out is not None else None,
+        code = _dtype_code(psi0, emulated)
+        p0 = _dev_ptr(psi0, n)
+        pout = _dev_ptr(psi_out, n, psi0.dtype) if psi_out is not None else None
+        _check(load().kry_evolve(self._h, code, p0, tp, t.size, m, tol, pout,
                                  P.ctypes.data_as(_dp), ctypes.byref(st), _stream(stream)))
         return P.reshape(t.size, self.K) if self.K > 1 else P, st.as_dict()
 
@@ -361,8 +375,9 @@ class Hamiltonian:
             _check(load().kry_set_workspace(self._h, None, 0))
             self._ws = None
             return
+        ptr = _dev_ptr(buf)
         nbytes = buf.numel() * buf.element_size()
-        _check(load().kry_set_workspace(self._h, ctypes.c_void_p(buf.data_ptr()), nbytes))
+        _check(load().kry_set_workspace(self._h, ptr, nbytes))
         self._ws = buf
 
     def close(self):

@@ -74,3 +74,29 @@ def test_sources_target_sm103a_only():
     f = build.flags()
     assert "arch=compute_103a,code=sm_103a" in f
     assert not any("sm_90" in x or "sm_100" in x for x in f)
+
+
+def test_binding_refuses_tensors_the_kernels_would_overrun():
+    """The binding hands the library only tensors of the element type and size it will read
+    or write: a complex64 output for a complex128 input, int32 states or int64 ranks would
+    send a kernel past the end of the buffer, so they are refused before any call."""
+    import torch
+    import paper_1704_02770_gb300 as k
+    with pytest.raises(TypeError):
+        k._dev_ptr(torch.zeros(4, dtype=torch.complex64), 4, torch.complex128)
+    with pytest.raises(TypeError):
+        k._dev_ptr(torch.zeros(4, dtype=torch.int32), dtype=torch.int64)
+    with pytest.raises(TypeError):
+        k._dev_ptr(torch.zeros(4, dtype=torch.int64), dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA"):        # the right type, but host memory
+        k._dev_ptr(torch.zeros(4, dtype=torch.int64), dtype=torch.int64)
+    with pytest.raises(TypeError):
+        k._dtype_code(torch.zeros(4, dtype=torch.float64))
+    # the checks run before the library is called: a stub Hamiltonian whose handle is unset
+    H = object.__new__(k.Hamiltonian)
+    H._h, H.K = None, 1
+    H.basis = type("B", (), {"dim": 4})()
+    with pytest.raises(ValueError, match="CUDA"):
+        H.apply(torch.zeros(4, dtype=torch.complex128))
+    with pytest.raises(TypeError):
+        H.evolve(torch.zeros(4, dtype=torch.float32), [1.0])
