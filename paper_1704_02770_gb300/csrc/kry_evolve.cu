@@ -455,7 +455,7 @@ int evolve_t(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool g
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
         const bool plain = plain_step_graph(H);
         st->n_launches = launched * (nk + (plain ? 2 * m : 0) + (ea.Yout ? 1 : 0) + ((opt && opt->ckpt) ? 1 : 0)) +
-                         (plain ? 0 : 2 * hp->n_c1) + 1;
+                         (plain ? 0 : 2 * hp->n_c1) + 1 + (FF && general ? 1 : 0) + (FF && d_psi_out ? 1 : 0);
         st->n_second_dots = hp->n_c1;
     }
     if (opt && opt->ckpt) {
@@ -739,7 +739,7 @@ int evolve_bt(kry_ham_s *H, int dtype, const void *d_psi0, uint64_t state, bool 
         st->max_orth_loss = *std::max_element(orth.begin(), orth.end());
         st->time_ms = ms;
         st->algo_bytes = hp->vec_passes * (double)nvec * (double)es;
-        st->n_launches = launched * (9 * m + 5) + (general ? 2 : 1);
+        st->n_launches = launched * (10 * m + 5) + (general ? 2 : 1) + (FF && general ? 1 : 0) + (FF && d_psi_out ? 1 : 0);
         st->n_second_dots = 0;
     }
     return KRY_OK;

@@ -129,3 +129,21 @@ def test_float_float_batch_against_fp64_batch(kry):
     Hc = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, np.tile(h[0], (3, 1)))
     Pc, _ = Hc.return_probability(st, times, dtype="c128e")
     assert np.max(np.abs(Pc - P1[:, None])) <= 1e-12
+
+
+def test_launch_count_batched(kry):
+    """Per Lanczos index the batched step launches ten kernels (the H.v, the dots, the update,
+    the two of the second pass, four partial-sum reductions and the refresh of the running
+    Krylov dimension over the realisations);
+    then the two of the small exponential, the combine, its reduction and the step
+    bookkeeping: 10 m + 5 per replay, plus the initial basis state."""
+    L, N, K, m = 12, 6, 8, 30
+    H = kry.Hamiltonian(kry.Basis(L, N), 1.0, 1.0, _fields(L, 1.5, 3, K))
+    st = workloads.neel_state(L)
+    H.return_probability(st, [0.1])   # capture
+    H.profile(True)
+    _, s = H.return_probability(st, [0.5, 2.0, 5.0], m=m, tol=1e-10)
+    steps = H.profile_read()["smallexp"]["launches"]
+    H.profile(False)
+    assert steps >= s["n_krylov_steps"] > 0
+    assert s["n_launches"] == steps * (10 * m + 5) + 1
